@@ -1,0 +1,224 @@
+/* mem.h — C ABI of the GB300 multi-modal elevation-mapping library.
+ *
+ * Implements the data-parallel map update of "MEM: Multi-Modal Elevation
+ * Mapping for Robotics and Learning" (arXiv 2309.16818):
+ *   - Sec. III-B (Data association): points -> cells by their horizontal
+ *     coordinates; cells -> pixels by pinhole projection with a Bresenham
+ *     visibility check against the height map;
+ *   - the height update the paper inherits from its predecessor (per-cell
+ *     Kalman update with an outlier gate, Table I rows "point trsf. & z err.
+ *     cnt" and "height update");
+ *   - Sec. III-C (Fusion algorithms): Latest (Eq. 1), Exponential averaging
+ *     (Eq. 2), Gaussian Bayesian inference (Eqs. 3-7), Dirichlet Bayesian
+ *     inference (Eqs. 8-12), and a class-max layer (Sec. V-B's
+ *     "highest class probability" colouring).
+ *
+ * Memory and streams
+ *   - The library owns every map's device memory (allocated in
+ *     mem_create_map, freed in mem_destroy_map).
+ *   - Every other pointer argument is caller-owned DEVICE memory unless the
+ *     argument says "host"; it must stay valid until the work queued on
+ *     `stream` has finished. The library never frees caller memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream). All calls are asynchronous on that stream. Calls on one map
+ *     must be ordered (issue them on one stream, or order them yourself).
+ *   - Layouts: points are float32 xyz rows [N][3] in the SENSOR frame; a
+ *     point source is [N][C] rows; an image source is HWC [H][Wi][C]; poses
+ *     are row-major 4x4 float64 (host) mapping sensor (or optical camera:
+ *     x right, y down, z forward) coordinates to world coordinates.
+ *
+ * Errors
+ *   - Argument errors are detected on the host before anything is queued;
+ *     they change no state and return MEM_ERR_ARG.
+ *   - CUDA launch errors return MEM_ERR_CUDA.
+ *   - Device-side failures (a bounded wait that ran out) set an error word in
+ *     the map; mem_check() synchronises and reports it as MEM_ERR_TIMEOUT.
+ *   - mem_last_error() returns a thread-local message for the last failure.
+ */
+#ifndef MEM_H
+#define MEM_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MEM_MAX_LAYERS 16
+#define MEM_MAX_SOURCES 8
+#define MEM_MAX_SOURCE_LAYERS 8
+
+typedef struct mem_map mem_map; /* opaque */
+
+typedef enum {
+  MEM_OK = 0,
+  MEM_ERR_ARG = 1,
+  MEM_ERR_CUDA = 2,
+  MEM_ERR_OOM = 3,
+  MEM_ERR_TIMEOUT = 4,
+  MEM_ERR_STATE = 5
+} mem_status;
+
+/* Per-layer fusion rule (Sec. III-C). For a point cloud, the N_j points of
+ * cell j in one call are one observation set; for an image, N_j = 1.
+ *   LATEST    theta = mean of the observations (Eq. 1)
+ *   EXPAVG    theta = w * mean + (1 - w) * theta_prev (Eq. 2); the first
+ *             observation of a cell sets theta = mean
+ *   GAUSS     mu, sigma^2 of the conjugate Gaussian update with known
+ *             observation variance var_meas (Eqs. 6-7); the first observation
+ *             has an infinitely wide prior (mu = mean, sigma^2 = var_meas / N)
+ *   DIRICHLET alpha += sum of the observations (Eq. 12), alpha starts at
+ *             alpha0; the class probabilities are alpha / sum(alpha) (Eq. 11)
+ *   CLASSMAX  (class id, confidence) of the largest class probability seen in
+ *             this call, smallest class index on ties; replaces the cell */
+typedef enum {
+  MEM_RULE_LATEST = 0,
+  MEM_RULE_EXPAVG = 1,
+  MEM_RULE_GAUSS = 2,
+  MEM_RULE_DIRICHLET = 3,
+  MEM_RULE_CLASSMAX = 4
+} mem_rule;
+
+typedef enum { MEM_F32 = 0, MEM_BF16 = 1, MEM_F16 = 2, MEM_U8 = 3 } mem_dtype;
+
+/* A multi-modal layer ("task-agnostic information container", Sec. III-A).
+ * channels = K classes or d feature dimensions of the observations.
+ * dtype    = storage of the layer values (MEM_F32, MEM_BF16 or MEM_F16);
+ *            accumulation is float32 whatever the storage. CLASSMAX and
+ *            DIRICHLET layers must be MEM_F32. */
+typedef struct {
+  int32_t channels;
+  int32_t dtype;
+  int32_t rule;
+  float w;        /* EXPAVG weight of the new observation                 */
+  float var_meas; /* GAUSS known observation variance sigma_f^2           */
+  float alpha0;   /* DIRICHLET prior concentration per class              */
+} mem_layer_desc;
+
+/* Map configuration. W even, 2 <= W <= 16384; n_maps >= 1 maps of the same
+ * shape live in one object (the batched path). Height model: measurement
+ * std s = sigma0 + sigma1 * range; a point is an outlier of a valid cell
+ * when (z - h)^2 > gate_lambda^2 (sigma_h^2 + s^2). */
+typedef struct {
+  int32_t W;
+  int32_t n_maps;
+  double res;      /* cell side (m); cells use float32(res), moves use res */
+  int32_t n_layers;
+  mem_layer_desc layers[MEM_MAX_LAYERS];
+  float sigma0, sigma1;
+  float gate_lambda;
+  float outlier_var; /* added to sigma_h^2 per rejected point              */
+  float time_var;    /* added to sigma_h^2 of every valid cell per call    */
+  float range_min, range_max;
+  float z_near;      /* camera near plane (m)                              */
+  int64_t max_points; /* initial point capacity of the per-call scratch    */
+} mem_map_config;
+
+/* One input source: a row of `channels` values per point (point clouds) or
+ * per pixel (images), fused into each listed layer in order. */
+typedef struct {
+  const void *data; /* device; [N][channels] or [H][Wi][channels]            */
+  int32_t dtype;    /* mem_dtype of the rows                                 */
+  int32_t channels;
+  int32_t n_layers;
+  int32_t layers[MEM_MAX_SOURCE_LAYERS];
+} mem_source;
+
+/* Geometric layer ids for mem_get_layer / mem_set_layer (part ignored). */
+#define MEM_LAYER_HEIGHT (-1)   /* float32 elevation h                    */
+#define MEM_LAYER_VARIANCE (-2) /* float32 elevation variance sigma_h^2   */
+#define MEM_LAYER_VALID (-3)    /* uint8 1 once a height was fused        */
+#define MEM_LAYER_NACC (-4)     /* uint32 accepted points, cumulative     */
+#define MEM_LAYER_NREJ (-5)     /* uint32 rejected (outlier) points       */
+
+/* Parts of a multi-modal layer. */
+#define MEM_PART_VALUE 0    /* storage dtype, S values per cell (S = channels;
+                               CLASSMAX: 2 = {class id as float, confidence}) */
+#define MEM_PART_THETA 1    /* DIRICHLET: float32 alpha / sum(alpha), K per cell */
+#define MEM_PART_VAR 2      /* GAUSS: float32 sigma^2, one per cell            */
+#define MEM_PART_OBSERVED 3 /* uint8, 1 once the layer of the cell was fused   */
+
+/* Create `cfg->n_maps` maps centred on the world origin, every cell empty.
+ * Returns MEM_ERR_ARG for an invalid config, MEM_ERR_OOM if device memory
+ * runs out. */
+mem_status mem_create_map(const mem_map_config *cfg, mem_map **out);
+mem_status mem_destroy_map(mem_map *m);
+
+/* Robot-centric re-centring (the map follows the robot): shift map
+ * `map_index` by whole cells so its centre is the cell centre nearest to
+ * robot_xy (host, world metres); cells that enter are reset. O(entering
+ * cells) on the device. */
+mem_status mem_move_map(mem_map *m, int32_t map_index, const double robot_xy[2], void *stream);
+
+/* Fuse one point cloud into a single-map object (n_maps == 1).
+ *   n        number of points (0 allowed), n < 2^30
+ *   xyz      device float32 [n][3], sensor frame; non-finite rows are dropped
+ *   sources  host array of n_sources (<= MEM_MAX_SOURCES) descriptors whose
+ *            `data` are device [n][channels] rows
+ *   T_map_sensor host float64 4x4 sensor -> world
+ * Steps: transform + range filter + cell key; stable radix sort of the keys;
+ * per-cell height update with outlier gate; per-layer fusion rules. */
+mem_status mem_fuse_pointcloud(mem_map *m, int64_t n, const float *xyz, int32_t n_sources,
+                               const mem_source *sources, const double T_map_sensor[16],
+                               void *stream);
+
+/* Fuse n_maps independent clouds into the n_maps maps of one object in one
+ * pass. offsets: host int64 [n_maps + 1] CSR offsets into xyz and the
+ * source rows; T_map_sensor: host float64 [n_maps][16]. Results equal
+ * n_maps separate single-map fuses. */
+mem_status mem_fuse_pointcloud_batch(mem_map *m, const int64_t *offsets, const float *xyz,
+                                     int32_t n_sources, const mem_source *sources,
+                                     const double *T_map_sensor, void *stream);
+
+/* Fuse one camera image (Sec. III-B, Fig. 2): every valid cell of map
+ * `map_index` is projected at its height into the pinhole camera
+ * K = {fx, fy, cx, cy} (host) with pose T_map_cam (host, optical frame ->
+ * world); it is visible iff in front of z_near, inside the image, and every
+ * valid cell on the Bresenham line from the camera's cell lies strictly
+ * below the ray. Visible cells fuse their pixel (one observation).
+ * vis_out (uint8 [W*W]) and pix_out (int32 [W*W], py*Wi+px or -1) are
+ * optional device outputs in logical cell order (row iy, column ix). */
+mem_status mem_fuse_image(mem_map *m, int32_t map_index, int32_t H, int32_t Wi, int32_t n_sources,
+                          const mem_source *sources, const double K[4], const double T_map_cam[16],
+                          uint8_t *vis_out, int32_t *pix_out, void *stream);
+
+/* Copy one layer (part) of map `map_index` into device memory `dst`, in
+ * logical cell order (cell j = iy * W + ix, values per cell contiguous). */
+mem_status mem_get_layer(mem_map *m, int32_t map_index, int32_t layer, int32_t part, void *dst,
+                         void *stream);
+/* Inverse of mem_get_layer (MEM_PART_THETA not settable): checkpoint restore
+ * and test fixtures. */
+mem_status mem_set_layer(mem_map *m, int32_t map_index, int32_t layer, int32_t part,
+                         const void *src, void *stream);
+/* World xy of the centre of map `map_index` (host output). */
+mem_status mem_get_origin(const mem_map *m, int32_t map_index, double out_xy[2]);
+/* Synchronise `stream` and report (then clear) the map's device error word. */
+mem_status mem_check(mem_map *m, void *stream);
+
+/* Schedule of the point path (no effect on results beyond the float32
+ * summation order inside a cell): radix_bits in [8, 10] is the digit width
+ * of the key sort; cells with at most small_max points are fused by one
+ * thread, longer runs by one warp; blocks_per_sm sizes the persistent grids.
+ * Synchronises the device. */
+mem_status mem_set_tuning(mem_map *m, int32_t radix_bits, int32_t small_max, int32_t blocks_per_sm);
+/* out = {radix_bits, small_max, blocks_per_sm, radix passes} (host). */
+mem_status mem_get_tuning(const mem_map *m, int32_t out[4]);
+
+/* Per-kernel timing: with profiling on, every launch group of this map is
+ * bracketed by CUDA events on its stream (graph replay is then disabled).
+ * mem_get_profile waits for the recorded events and returns, per slot, the
+ * summed milliseconds and the number of launches since the previous read:
+ * 0 transform+key, 1 digit scan, 2 radix passes, 3 segments, 4 short-cell
+ * fuse, 5 long-cell fuse, 6 time variance, 7 image fuse, 8 move. */
+#define MEM_PROFILE_SLOTS 16
+mem_status mem_set_profiling(mem_map *m, int32_t on);
+mem_status mem_get_profile(mem_map *m, double ms[MEM_PROFILE_SLOTS], int64_t calls[MEM_PROFILE_SLOTS]);
+/* Synchronise `stream`; out = {short cells, long cells, kept points, radix
+ * passes} of the last point fuse (host output). */
+mem_status mem_get_stats(mem_map *m, void *stream, int64_t out[4]);
+/* Thread-local description of the last error. */
+const char *mem_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,84 @@
+// Host-side map object shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "mem_internal.cuh"
+
+namespace memh {
+
+constexpr int kJobSlots = 8;
+
+struct Tuning {
+  int radix_bits = 9;   // digit width of the radix sort (8..10)
+  int small_max = 8;    // segments up to this many points: one thread each
+  int blocks_per_sm = 4;
+};
+
+struct Map {
+  mem_map_config cfg;
+  memk::MapDev md;
+  Tuning tune;
+  int passes = 1;
+  int key_bits = 1;
+  int n_sm = 148;
+  int device = 0;
+  std::vector<double> origin;  // [n_maps][2] world xy of each map centre
+  std::vector<int> ring;       // [n_maps][2] ring-buffer offsets (physical = logical + ring mod W)
+  // device job block and pinned staging slots
+  char* d_job = nullptr;
+  size_t job_bytes = 0;
+  char* h_job[kJobSlots] = {};
+  cudaEvent_t job_ev[kJobSlots] = {};
+  int job_slot = 0;
+  // CUDA graph of the batched point path
+  cudaGraphExec_t graph = nullptr;
+  cudaStream_t graph_stream = nullptr;
+  bool use_graph = true;
+  // optional per-kernel timing (CUDA events around each launch group)
+  bool prof_on = false;
+  struct ProfMark {
+    int slot;
+    cudaEvent_t a, b;
+  };
+  std::vector<ProfMark> prof_pending;
+  double prof_ms[16] = {};
+  int64_t prof_calls[16] = {};
+  // allocations to free
+  std::vector<void*> allocs;
+  std::vector<void*> scratch_allocs;
+};
+
+// profile slots
+enum { kProfKey = 0, kProfDigits, kProfSort, kProfSegments, kProfFuseSmall, kProfFuseLarge,
+       kProfTime, kProfImage, kProfMove, kProfSlots };
+
+// Brackets a launch group with events when profiling is on.
+struct ProfScope {
+  Map* m;
+  int slot;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr;
+  ProfScope(Map* m_, int slot_, cudaStream_t st_) : m(m_), slot(slot_), st(st_) {
+    if (m->prof_on) {
+      cudaEventCreate(&a);
+      cudaEventRecord(a, st);
+    }
+  }
+  ~ProfScope() {
+    if (a) {
+      cudaEvent_t b;
+      cudaEventCreate(&b);
+      cudaEventRecord(b, st);
+      m->prof_pending.push_back({slot, a, b});
+    }
+  }
+};
+
+cudaError_t alloc_scratch(Map* m, int64_t cap);
+void free_scratch(Map* m);
+int key_bits_for(const Map* m);
+cudaError_t prepare_kernels();
+
+}  // namespace memh

@@ -1,0 +1,251 @@
+// Internal device-side structures and helpers of the mapping library.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/mem.h"
+
+namespace memk {
+
+typedef uint32_t u32;
+typedef uint64_t u64;
+
+constexpr int kMaxLayers = MEM_MAX_LAYERS;
+constexpr int kMaxSources = MEM_MAX_SOURCES;
+constexpr int kMaxSrcLayers = MEM_MAX_SOURCE_LAYERS;
+constexpr u32 kFlagValid = 1u;               // bit 0: height valid
+constexpr u32 kSpinLimit = 1u << 22;         // bounded waits (x ~100 ns each)
+constexpr int kDevErrTimeout = 1;
+
+// Per-layer static description (device copy of mem_layer_desc + derived).
+struct LayerDev {
+  int C;        // channels of the observations
+  int S;        // stored values per cell
+  int dtype;    // storage
+  int rule;
+  float w, one_minus_w, var_meas, alpha0;
+  void* data;   // [cells][S]
+  float* gvar;  // GAUSS: [cells]
+};
+
+// Everything about a map object that does not change between calls.
+struct MapDev {
+  int W, n_maps;
+  u32 W2;        // W*W
+  u32 sentinel;  // n_maps * W2: key of dropped points
+  float res;
+  float sigma0, sigma1, lam2, outlier_var, time_var, range_min, range_max, z_near;
+  int n_layers;
+  LayerDev L[kMaxLayers];
+  float* h;
+  float* var;
+  u32* flags;  // bit0 valid, bit (1 + l) layer l observed
+  u32* n_acc;
+  u32* n_rej;
+  // scratch of the point path
+  u32 *keys0, *keys1, *vals0, *vals1;
+  u32* hist;        // [passes][radix] digit counts, then exclusive offsets
+  u32* lookback;    // [passes][tiles][radix]
+  u32* counters;    // [0..3] tile counters per pass, [4] n_small, [5] n_large
+  uint2* seg_small; // (start, end)
+  uint2* seg_large;
+  int* err;
+  int64_t cap;      // point capacity of the scratch
+  int64_t cap_tiles;
+};
+
+// Per-map, per-call parameters.
+struct MapCall {
+  float R[9];  // rotation (point path: sensor -> map; image path: map -> camera)
+  float t[3];  // translation relative to the map centre
+  int ring_x, ring_y;
+  float cam_x, cam_y, cam_h;  // image path: camera position relative to the map centre
+  float pad;
+};
+
+struct SrcDev {
+  const void* data;
+  int dtype, C, n_layers;
+  int layers[kMaxSrcLayers];
+  int vec_ok;  // data is 16-byte aligned: rows may be read with vector loads
+};
+
+// Per-call job of the point path, resident in device memory so the whole
+// kernel sequence can be replayed from a CUDA graph.
+struct PointJob {
+  int64_t n;
+  const float* xyz;
+  const int64_t* offsets;  // [n_maps + 1] or nullptr for one map
+  const MapCall* maps;     // [n_maps]
+  int n_maps;
+  int n_src;
+  SrcDev src[kMaxSources];
+};
+
+// ---------------------------------------------------------------------------
+// numeric helpers: fixed IEEE sequences (never contracted by the compiler)
+
+struct PointEval {
+  float z, vm;
+  int ix, iy;  // logical cell
+  bool keep;
+};
+
+// Transform, filter and associate one sensor-frame point:
+//   p = R p_s + t (fmaf chain), range = sqrt(xs^2 + ys^2 + zs^2),
+//   cell = floor(x / res) + W/2, variance = (sigma0 + sigma1 range)^2.
+__device__ __forceinline__ PointEval eval_point(const MapDev& md, const MapCall& mc, float xs,
+                                                float ys, float zs) {
+  PointEval e;
+  e.keep = false;
+  e.ix = e.iy = 0;
+  e.z = e.vm = 0.f;
+  if (!(isfinite(xs) && isfinite(ys) && isfinite(zs))) return e;
+  float r2 = __fmaf_rn(xs, xs, __fmaf_rn(ys, ys, __fmul_rn(zs, zs)));
+  float rs = __fsqrt_rn(r2);
+  if (!(rs >= md.range_min && rs <= md.range_max)) return e;
+  float x = __fmaf_rn(mc.R[0], xs, __fmaf_rn(mc.R[1], ys, __fmaf_rn(mc.R[2], zs, mc.t[0])));
+  float y = __fmaf_rn(mc.R[3], xs, __fmaf_rn(mc.R[4], ys, __fmaf_rn(mc.R[5], zs, mc.t[1])));
+  float z = __fmaf_rn(mc.R[6], xs, __fmaf_rn(mc.R[7], ys, __fmaf_rn(mc.R[8], zs, mc.t[2])));
+  float qx = floorf(__fdiv_rn(x, md.res));
+  float qy = floorf(__fdiv_rn(y, md.res));
+  float half = (float)(md.W / 2);
+  if (!(qx >= -half && qx < half && qy >= -half && qy < half)) return e;
+  float sm = __fmaf_rn(md.sigma1, rs, md.sigma0);
+  e.ix = (int)qx + md.W / 2;
+  e.iy = (int)qy + md.W / 2;
+  e.z = z;
+  e.vm = __fmul_rn(sm, sm);
+  e.keep = true;
+  return e;
+}
+
+__device__ __forceinline__ u32 phys_cell(const MapDev& md, const MapCall& mc, int ix, int iy) {
+  int px = ix + mc.ring_x;
+  if (px >= md.W) px -= md.W;
+  int py = iy + mc.ring_y;
+  if (py >= md.W) py -= md.W;
+  return (u32)py * (u32)md.W + (u32)px;
+}
+
+// Outlier gate of the height update: reject iff (z - h)^2 > lambda^2 (var_h + vm).
+__device__ __forceinline__ bool gate_reject(float z, float h, float var_h, float vm, float lam2) {
+  float d = __fsub_rn(z, h);
+  float lhs = __fmul_rn(d, d);
+  float rhs = __fmul_rn(lam2, __fadd_rn(var_h, vm));
+  return lhs > rhs;
+}
+
+// ---------------------------------------------------------------------------
+// loads / stores of source rows and layer values
+
+__device__ __forceinline__ float ld_any(const void* base, int dtype, int64_t off) {
+  switch (dtype) {
+    case MEM_F32: return __ldg((const float*)base + off);
+    case MEM_BF16: return __bfloat162float(((const __nv_bfloat16*)base)[off]);
+    case MEM_F16: return __half2float(((const __half*)base)[off]);
+    default: return (float)__ldg((const unsigned char*)base + off);
+  }
+}
+
+// Four consecutive channels c0..c0+3 of row `row` (channels >= C read as 0).
+__device__ __forceinline__ void ld_src4(const SrcDev& s, int64_t row, int c0, float v[4]) {
+  const int64_t off = row * s.C + c0;
+  const int nc = min(4, s.C - c0);
+  if (s.vec_ok && nc == 4 && (off & 3) == 0) {
+    if (s.dtype == MEM_F32) {
+      float4 q = __ldg((const float4*)((const float*)s.data + off));
+      v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+      return;
+    }
+    if (s.dtype == MEM_BF16) {
+      uint2 q = __ldg((const uint2*)((const __nv_bfloat16*)s.data + off));
+      __nv_bfloat162 a = *reinterpret_cast<__nv_bfloat162*>(&q.x);
+      __nv_bfloat162 b = *reinterpret_cast<__nv_bfloat162*>(&q.y);
+      float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
+      v[0] = fa.x; v[1] = fa.y; v[2] = fb.x; v[3] = fb.y;
+      return;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) v[k] = k < nc ? ld_any(s.data, s.dtype, off + k) : 0.f;
+}
+
+__device__ __forceinline__ float ld_layer(const LayerDev& L, int64_t off) {
+  switch (L.dtype) {
+    case MEM_BF16: return __bfloat162float(((const __nv_bfloat16*)L.data)[off]);
+    case MEM_F16: return __half2float(((const __half*)L.data)[off]);
+    default: return ((const float*)L.data)[off];
+  }
+}
+
+__device__ __forceinline__ void st_layer(const LayerDev& L, int64_t off, float v) {
+  switch (L.dtype) {
+    case MEM_BF16: ((__nv_bfloat16*)L.data)[off] = __float2bfloat16_rn(v); break;
+    case MEM_F16: ((__half*)L.data)[off] = __float2half_rn(v); break;
+    default: ((float*)L.data)[off] = v;
+  }
+}
+
+// Apply one rule to channel c of cell g from N observations with sum S
+// (and, for the Gaussian rule, the cell's prior variance s02; obs = observed).
+// CLASSMAX is handled by the callers (needs the whole row).
+__device__ __forceinline__ void apply_rule_ch(const LayerDev& L, int64_t g, int c, float N,
+                                              float S, bool obs, float s02) {
+  const int64_t off = g * L.S + c;
+  switch (L.rule) {
+    case MEM_RULE_LATEST: st_layer(L, off, __fdiv_rn(S, N)); break;
+    case MEM_RULE_EXPAVG: {
+      float a = __fdiv_rn(S, N);
+      float t = obs ? __fmaf_rn(L.w, a, __fmul_rn(L.one_minus_w, ld_layer(L, off))) : a;
+      st_layer(L, off, t);
+      break;
+    }
+    case MEM_RULE_GAUSS: {
+      float mu;
+      if (obs) {
+        float den = __fmaf_rn(N, s02, L.var_meas);
+        mu = __fdiv_rn(__fmaf_rn(L.var_meas, ld_layer(L, off), __fmul_rn(s02, S)), den);
+      } else {
+        mu = __fdiv_rn(S, N);
+      }
+      st_layer(L, off, mu);
+      break;
+    }
+    case MEM_RULE_DIRICHLET: st_layer(L, off, __fadd_rn(ld_layer(L, off), S)); break;
+    default: break;
+  }
+}
+
+__device__ __forceinline__ float gauss_new_var(const LayerDev& L, float N, bool obs, float s02) {
+  return obs ? __fdiv_rn(__fmul_rn(L.var_meas, s02), __fmaf_rn(N, s02, L.var_meas))
+             : __fdiv_rn(L.var_meas, N);
+}
+
+// relaxed device-scope loads/stores for the radix-sort look-back
+__device__ __forceinline__ u32 ld_relaxed(const u32* p) {
+  u32 v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed(u32* p, u32 v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+}  // namespace memk
+
+// host-side launchers (defined in the .cu files)
+namespace memh {
+struct Map;
+cudaError_t launch_point_fuse(Map* m, const memk::PointJob* d_job, cudaStream_t st);
+cudaError_t launch_image_fuse(Map* m, int map_index, const memk::MapCall& mc, int H, int Wi,
+                              int n_src, const memk::SrcDev* src, const float K[4],
+                              uint8_t* vis, int32_t* pix, cudaStream_t st);
+cudaError_t launch_clear_entering(Map* m, int map_index, int sx, int sy, int ring_x, int ring_y,
+                                  cudaStream_t st);
+cudaError_t launch_layer_copy(Map* m, int map_index, int layer, int part, void* buf, bool to_map,
+                              cudaStream_t st);
+cudaError_t launch_init_state(Map* m, cudaStream_t st);
+}  // namespace memh

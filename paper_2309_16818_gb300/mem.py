@@ -1,0 +1,277 @@
+"""Python binding of ``libmem.so`` (include/mem.h): argument marshalling only.
+
+Device memory and streams come from PyTorch; every step of the map update runs
+in the library's CUDA kernels. Importing this module does not need a GPU, but
+loading the library does need it built (``paper_2309_16818_gb300.build``); a
+missing library raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmem.so")
+
+MAX_LAYERS, MAX_SOURCES, MAX_SOURCE_LAYERS = 16, 8, 8
+OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_TIMEOUT, ERR_STATE = range(6)
+LATEST, EXPAVG, GAUSS, DIRICHLET, CLASSMAX = range(5)
+F32, BF16, F16, U8 = range(4)
+LAYER_HEIGHT, LAYER_VARIANCE, LAYER_VALID, LAYER_NACC, LAYER_NREJ = -1, -2, -3, -4, -5
+PART_VALUE, PART_THETA, PART_VAR, PART_OBSERVED = range(4)
+
+EXPORTS = ["mem_create_map", "mem_destroy_map", "mem_move_map", "mem_fuse_pointcloud",
+           "mem_fuse_pointcloud_batch", "mem_fuse_image", "mem_get_layer", "mem_set_layer",
+           "mem_get_origin", "mem_check", "mem_last_error", "mem_set_tuning", "mem_get_tuning",
+           "mem_set_profiling", "mem_get_profile", "mem_get_stats"]
+PROFILE_SLOTS = ["key", "digit_scan", "radix_sort", "segments", "fuse_small", "fuse_large",
+                 "time_var", "image", "move"]
+
+
+class LayerDesc(C.Structure):
+    _fields_ = [("channels", C.c_int32), ("dtype", C.c_int32), ("rule", C.c_int32),
+                ("w", C.c_float), ("var_meas", C.c_float), ("alpha0", C.c_float)]
+
+
+class MapConfig(C.Structure):
+    _fields_ = [("W", C.c_int32), ("n_maps", C.c_int32), ("res", C.c_double),
+                ("n_layers", C.c_int32), ("layers", LayerDesc * MAX_LAYERS),
+                ("sigma0", C.c_float), ("sigma1", C.c_float), ("gate_lambda", C.c_float),
+                ("outlier_var", C.c_float), ("time_var", C.c_float), ("range_min", C.c_float),
+                ("range_max", C.c_float), ("z_near", C.c_float), ("max_points", C.c_int64)]
+
+
+class Source(C.Structure):
+    _fields_ = [("data", C.c_void_p), ("dtype", C.c_int32), ("channels", C.c_int32),
+                ("n_layers", C.c_int32), ("layers", C.c_int32 * MAX_SOURCE_LAYERS)]
+
+
+class MemError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    """Load ``libmem.so``; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -m paper_2309_16818_gb300.build`")
+        L = C.CDLL(LIB_PATH)
+        P, I32, I64 = C.c_void_p, C.c_int32, C.c_int64
+        sig = {
+            "mem_create_map": [P, P], "mem_destroy_map": [P],
+            "mem_move_map": [P, I32, P, P],
+            "mem_fuse_pointcloud": [P, I64, P, I32, P, P, P],
+            "mem_fuse_pointcloud_batch": [P, P, P, I32, P, P, P],
+            "mem_fuse_image": [P, I32, I32, I32, I32, P, P, P, P, P, P],
+            "mem_get_layer": [P, I32, I32, I32, P, P], "mem_set_layer": [P, I32, I32, I32, P, P],
+            "mem_get_origin": [P, I32, P], "mem_check": [P, P], "mem_last_error": [],
+            "mem_set_tuning": [P, I32, I32, I32], "mem_get_tuning": [P, P],
+            "mem_set_profiling": [P, I32], "mem_get_profile": [P, P, P], "mem_get_stats": [P, P, P],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = C.c_char_p if name == "mem_last_error" else C.c_int
+        _lib = L
+    return _lib
+
+
+def _ck(status):
+    if status != OK:
+        raise MemError(status, lib().mem_last_error().decode())
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _dtype_code(t) -> int:
+    torch = _torch()
+    m = {torch.float32: F32, torch.bfloat16: BF16, torch.float16: F16, torch.uint8: U8}
+    if t.dtype not in m:
+        raise TypeError(f"unsupported dtype {t.dtype}")
+    return m[t.dtype]
+
+
+def _stream(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _pose(T, n=1):
+    a = np.ascontiguousarray(np.asarray(T, dtype=np.float64).reshape(n * 16))
+    return a
+
+
+@dataclass
+class Layer:
+    channels: int
+    rule: int
+    dtype: int = F32
+    w: float = 0.1
+    var_meas: float = 1.0
+    alpha0: float = 1.0
+
+    @property
+    def stored(self) -> int:
+        return 2 if self.rule == CLASSMAX else self.channels
+
+
+class Map:
+    """A set of ``n_maps`` robot-centric W x W maps with the given multi-modal layers."""
+
+    def __init__(self, W: int, res: float, layers=(), n_maps: int = 1, sigma0: float = 0.01,
+                 sigma1: float = 0.002, gate_lambda: float = 2.0, outlier_var: float = 0.0,
+                 time_var: float = 0.0, range_min: float = 0.1, range_max: float = 50.0,
+                 z_near: float = 0.05, max_points: int = 1 << 20):
+        cfg = MapConfig()
+        cfg.W, cfg.n_maps, cfg.res = W, n_maps, res
+        self.layers = list(layers)
+        cfg.n_layers = len(self.layers)
+        for i, L in enumerate(self.layers):
+            d = cfg.layers[i]
+            d.channels, d.dtype, d.rule = L.channels, L.dtype, L.rule
+            d.w, d.var_meas, d.alpha0 = L.w, L.var_meas, L.alpha0
+        cfg.sigma0, cfg.sigma1, cfg.gate_lambda = sigma0, sigma1, gate_lambda
+        cfg.outlier_var, cfg.time_var = outlier_var, time_var
+        cfg.range_min, cfg.range_max, cfg.z_near = range_min, range_max, z_near
+        cfg.max_points = max_points
+        self.cfg = cfg
+        self.W, self.n_maps, self.res = W, n_maps, res
+        self._h = C.c_void_p()
+        _ck(lib().mem_create_map(C.byref(cfg), C.byref(self._h)))
+
+    def close(self):
+        if self._h:
+            lib().mem_destroy_map(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- inputs -------------------------------------------------------------------
+    def _sources(self, sources, keep):
+        arr = (Source * MAX_SOURCES)()
+        for i, (t, layers) in enumerate(sources):
+            assert t.is_cuda and t.is_contiguous()
+            keep.append(t)
+            arr[i].data = t.data_ptr()
+            arr[i].dtype = _dtype_code(t)
+            arr[i].channels = t.shape[-1]
+            arr[i].n_layers = len(layers)
+            for k, l in enumerate(layers):
+                arr[i].layers[k] = l
+        return arr
+
+    def fuse_pointcloud(self, xyz, T, sources=(), stream=None):
+        """xyz: cuda float32 [N,3] (sensor frame); sources: [(cuda [N,C] tensor, [layer ids])];
+        T: 4x4 sensor -> world (float64 host)."""
+        keep = []
+        src = self._sources(list(sources), keep)
+        n = int(xyz.shape[0])
+        _ck(lib().mem_fuse_pointcloud(self._h, n, C.c_void_p(xyz.data_ptr() if n else 0),
+                                      len(sources), src, _pose(T).ctypes.data, _stream(stream)))
+
+    def fuse_pointcloud_batch(self, offsets, xyz, T, sources=(), stream=None):
+        keep = []
+        src = self._sources(list(sources), keep)
+        off = np.ascontiguousarray(offsets, dtype=np.int64)
+        Tb = _pose(T, self.n_maps)
+        _ck(lib().mem_fuse_pointcloud_batch(self._h, off.ctypes.data,
+                                            C.c_void_p(xyz.data_ptr() if xyz.numel() else 0),
+                                            len(sources), src, Tb.ctypes.data, _stream(stream)))
+
+    def fuse_image(self, H, Wi, K, T, sources=(), map_index=0, vis=None, pix=None, stream=None):
+        keep = []
+        src = self._sources(list(sources), keep)
+        Kd = np.ascontiguousarray(K, dtype=np.float64)
+        _ck(lib().mem_fuse_image(self._h, map_index, H, Wi, len(sources), src, Kd.ctypes.data,
+                                 _pose(T).ctypes.data,
+                                 C.c_void_p(vis.data_ptr() if vis is not None else 0),
+                                 C.c_void_p(pix.data_ptr() if pix is not None else 0),
+                                 _stream(stream)))
+
+    def move(self, robot_xy, map_index=0, stream=None):
+        xy = np.ascontiguousarray(robot_xy, dtype=np.float64)
+        _ck(lib().mem_move_map(self._h, map_index, xy.ctypes.data, _stream(stream)))
+
+    # -- state ----------------------------------------------------------------------
+    def _layer_shape(self, layer, part):
+        torch = _torch()
+        W2 = self.W * self.W
+        if layer < 0:
+            dt = {LAYER_HEIGHT: torch.float32, LAYER_VARIANCE: torch.float32,
+                  LAYER_VALID: torch.uint8, LAYER_NACC: torch.int32, LAYER_NREJ: torch.int32}[layer]
+            return (W2,), dt
+        L = self.layers[layer]
+        if part == PART_VALUE:
+            dt = {F32: torch.float32, BF16: torch.bfloat16, F16: torch.float16}[L.dtype]
+            return (W2, L.stored), dt
+        if part == PART_THETA:
+            return (W2, L.channels), torch.float32
+        if part == PART_VAR:
+            return (W2,), torch.float32
+        return (W2,), torch.uint8
+
+    def get_layer(self, layer, part=PART_VALUE, map_index=0, out=None, stream=None):
+        torch = _torch()
+        shape, dt = self._layer_shape(layer, part)
+        if out is None:
+            out = torch.empty(shape, dtype=dt, device="cuda")
+        _ck(lib().mem_get_layer(self._h, map_index, layer, part, C.c_void_p(out.data_ptr()),
+                                _stream(stream)))
+        return out
+
+    def set_layer(self, layer, src, part=PART_VALUE, map_index=0, stream=None):
+        shape, dt = self._layer_shape(layer, part)
+        assert src.is_cuda and src.is_contiguous() and src.dtype == dt and src.numel() == int(np.prod(shape))
+        _ck(lib().mem_set_layer(self._h, map_index, layer, part, C.c_void_p(src.data_ptr()),
+                                _stream(stream)))
+
+    def origin(self, map_index=0):
+        o = np.zeros(2)
+        _ck(lib().mem_get_origin(self._h, map_index, o.ctypes.data))
+        return float(o[0]), float(o[1])
+
+    def check(self, stream=None):
+        _ck(lib().mem_check(self._h, _stream(stream)))
+
+    def set_tuning(self, radix_bits, small_max, blocks_per_sm):
+        _ck(lib().mem_set_tuning(self._h, radix_bits, small_max, blocks_per_sm))
+
+    def get_tuning(self):
+        out = np.zeros(4, np.int32)
+        _ck(lib().mem_get_tuning(self._h, out.ctypes.data))
+        return dict(radix_bits=int(out[0]), small_max=int(out[1]), blocks_per_sm=int(out[2]),
+                    passes=int(out[3]))
+
+    def set_profiling(self, on: bool):
+        _ck(lib().mem_set_profiling(self._h, int(on)))
+
+    def get_profile(self):
+        """{slot name: (total ms, launch groups)} since the previous read."""
+        ms = np.zeros(16, np.float64)
+        calls = np.zeros(16, np.int64)
+        _ck(lib().mem_get_profile(self._h, ms.ctypes.data, calls.ctypes.data))
+        return {k: (float(ms[i]), int(calls[i])) for i, k in enumerate(PROFILE_SLOTS)}
+
+    def get_stats(self, stream=None):
+        out = np.zeros(4, np.int64)
+        _ck(lib().mem_get_stats(self._h, _stream(stream), out.ctypes.data))
+        return dict(short_cells=int(out[0]), long_cells=int(out[1]), kept=int(out[2]),
+                    passes=int(out[3]))

@@ -1,0 +1,173 @@
+"""CUDA point-cloud path (transform, radix binning, height update, fusion rules, move)
+against the oracle, element by element, through the C ABI."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2309_16818_gb300 import synth
+
+from helpers import (cloud_sources_gpu, cloud_sources_np, compare_states, cuda_xyz, gpu_state,
+                     make_pair, multimodal_layers, upload_state)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def test_config1_height_and_colour(torch):
+    c = synth.config1()
+    cl = c["cloud"]
+    layers = [dict(channels=3, rule=O.LATEST)]
+    g, o = make_pair(c["W"], c["res"], layers)
+    o.fuse_points(cl.xyz, cl.T, [(cl.rgb, [0])])
+    g.fuse_pointcloud(cuda_xyz(cl), cl.T, [(torch.from_numpy(cl.rgb).cuda(), [0])])
+    g.check()
+    gs = gpu_state(g)
+    assert o.valid.sum() > 10000
+    compare_states(gs, o, what="config 1")
+
+
+@pytest.mark.parametrize("radix_bits,small_max", [(8, 8), (9, 1), (10, 32), (9, 4)])
+def test_multimodal_scan_sequence(torch, radix_bits, small_max):
+    """Several poses of the multi-modal workload (reduced sensors), each step starting both
+    sides from the same (oracle) state: move, then fuse, then compare."""
+    c = synth.config2(n_poses=3, scale=0.25)
+    g, o = make_pair(c["W"], c["res"], multimodal_layers(), max_points=1 << 16)
+    g.set_tuning(radix_bits, small_max, 4)
+    for k, scan in enumerate(c["scans"]):
+        upload_state(g, o)
+        xy = c["poses"][k][:2]
+        o.move(xy)
+        g.move(xy)
+        assert g.origin() == o.origin
+        o.fuse_points(scan.xyz, scan.T, cloud_sources_np(scan))
+        g.fuse_pointcloud(cuda_xyz(scan), scan.T, cloud_sources_gpu(scan))
+        g.check()
+        compare_states(gpu_state(g), o, what=f"pose {k}")
+    assert o.valid.sum() > 2000 and o.n_rej.sum() > 0
+
+
+def test_full_size_multimodal_pose(torch):
+    """One full-size pose (128-beam LiDAR + 640x480 depth camera, 500x500 map), all cells."""
+    c = synth.config2(n_poses=2, scale=1.0)
+    g, o = make_pair(c["W"], c["res"], multimodal_layers())
+    for k, scan in enumerate(c["scans"]):
+        upload_state(g, o)
+        o.move(c["poses"][k][:2])
+        g.move(c["poses"][k][:2])
+        o.fuse_points(scan.xyz, scan.T, cloud_sources_np(scan))
+        g.fuse_pointcloud(cuda_xyz(scan), scan.T, cloud_sources_gpu(scan))
+        g.check()
+        compare_states(gpu_state(g), o, what=f"full pose {k}")
+
+
+def test_free_running_sequence_with_moves(torch):
+    """The CUDA map runs on its own over 4 poses (no state upload); integer results must match
+    except in cells where a gate decision sits within 1e-3 of its threshold."""
+    c = synth.config2(n_poses=4, scale=0.25)
+    g, o = make_pair(c["W"], c["res"], multimodal_layers())
+    W = c["W"]
+    near_cells = np.zeros(W * W, bool)
+    for k, scan in enumerate(c["scans"]):
+        o0 = o.origin
+        o.move(c["poses"][k][:2])
+        g.move(c["poses"][k][:2])
+        # the mask moves with the map: new cell (ix, iy) was old (ix + sx, iy + sy)
+        sx = round((o.origin[0] - o0[0]) / c["res"])
+        sy = round((o.origin[1] - o0[1]) / c["res"])
+        old = near_cells.reshape(W, W)
+        new = np.zeros_like(old)
+        ys, xs = np.mgrid[0:W, 0:W]
+        ok = (xs + sx >= 0) & (xs + sx < W) & (ys + sy >= 0) & (ys + sy < W)
+        new[ok] = old[(ys + sy)[ok], (xs + sx)[ok]]
+        near_cells = new.ravel()
+        r = o.fuse_points(scan.xyz, scan.T, cloud_sources_np(scan), want_cells=True, want_near=True)
+        near_cells[r["cells"][r["near"].astype(bool)]] = True
+        g.fuse_pointcloud(cuda_xyz(scan), scan.T, cloud_sources_gpu(scan))
+    g.check()
+    gs = gpu_state(g)
+    keep = ~near_cells
+    assert keep.sum() > 0.99 * keep.size
+    compare_states(gs, o, mask=keep, what="free running", )
+
+
+def test_deterministic_rerun(torch):
+    c = synth.config2(n_poses=1, scale=0.5)
+    scan = c["scans"][0]
+    outs = []
+    for _ in range(2):
+        g, _o = make_pair(c["W"], c["res"], multimodal_layers())
+        for _k in range(2):
+            g.fuse_pointcloud(cuda_xyz(scan), scan.T, cloud_sources_gpu(scan))
+        s = gpu_state(g)
+        outs.append(np.concatenate([s["h"], s["var"]] + [x.ravel() for x in s["layers"]]))
+    assert np.array_equal(outs[0].view(np.uint64), outs[1].view(np.uint64))
+
+
+def test_edge_cases(torch):
+    W, res = 50, 0.1   # W not a multiple of the 16-cell tiles
+    layers = [dict(channels=3, rule=O.LATEST), dict(channels=5, rule=O.GAUSS, var_meas=0.3)]
+    g, o = make_pair(W, res, layers)
+    T = np.eye(4)
+    T[2, 3] = 1.0
+    # empty cloud
+    g.fuse_pointcloud(torch.empty((0, 3), device="cuda"), T, [])
+    # all points dropped: NaN, out of range, out of map
+    bad = np.array([[np.nan, 0, -1], [0, np.inf, -1], [0.01, 0.0, 0.0], [10.0, 0.0, -1.0],
+                    [0.0, -2.51, -1.0]], np.float32)
+    rgb = np.zeros((5, 3), np.uint8)
+    f = np.zeros((5, 5), np.float32)
+    o.fuse_points(bad, T, [(rgb, [0]), (f, [1])])
+    g.fuse_pointcloud(torch.from_numpy(bad).cuda(), T,
+                      [(torch.from_numpy(rgb).cuda(), [0]), (torch.from_numpy(f).cuda(), [1])])
+    # one long run: 5000 points in one cell, points exactly on cell edges, ragged tail
+    rng = np.random.default_rng(0)
+    one = np.tile(np.array([[0.05, 0.05, -1.0]], np.float32), (5000, 1))
+    one[:, 2] += rng.normal(0, 0.01, 5000).astype(np.float32)
+    edges = (rng.integers(-25, 25, size=(3001, 2)) * 0.1).astype(np.float32)
+    edges = np.column_stack([edges, np.full(3001, -1.0, np.float32)])
+    pts = np.concatenate([one, edges, rng.uniform(-3, 3, size=(777, 3)).astype(np.float32)])
+    rgb = rng.integers(0, 256, size=(len(pts), 3), dtype=np.uint8)
+    f = rng.normal(size=(len(pts), 5)).astype(np.float32)
+    upload_state(g, o)
+    o.fuse_points(pts, T, [(rgb, [0]), (f, [1])])
+    g.fuse_pointcloud(torch.from_numpy(pts).cuda(), T,
+                      [(torch.from_numpy(rgb).cuda(), [0]), (torch.from_numpy(f).cuda(), [1])])
+    g.check()
+    compare_states(gpu_state(g), o, what="edge cases")
+    assert o.n_acc.max() + o.n_rej.max() >= 5000
+
+
+def test_time_and_outlier_variance(torch):
+    c = synth.config2(n_poses=2, scale=0.2)
+    g, o = make_pair(c["W"], c["res"], multimodal_layers(), outlier_var=0.01, time_var=1e-4)
+    for k, scan in enumerate(c["scans"]):
+        upload_state(g, o)
+        o.fuse_points(scan.xyz, scan.T, cloud_sources_np(scan))
+        g.fuse_pointcloud(cuda_xyz(scan), scan.T, cloud_sources_gpu(scan))
+        compare_states(gpu_state(g), o, what=f"variance growth pose {k}")
+
+
+def test_bf16_and_f16_feature_storage(torch):
+    """Gaussian feature layers stored in BF16 / F16 / F32, fed BF16 point features."""
+    c = synth.config4(n_maps=1, n_lo=40_000, n_hi=40_001)
+    cl = c["clouds"][0]
+    layers = [dict(channels=16, rule=O.GAUSS, var_meas=1.0, dtype=O.BF16),
+              dict(channels=16, rule=O.GAUSS, var_meas=1.0, dtype=O.F16),
+              dict(channels=16, rule=O.GAUSS, var_meas=1.0, dtype=O.F32),
+              dict(channels=3, rule=O.LATEST)]
+    g, o = make_pair(c["W"], c["res"], layers)
+    feat_t = torch.from_numpy(cl.feat.view(np.int16)).cuda().view(torch.bfloat16)
+    for k in range(3):
+        upload_state(g, o)
+        o.fuse_points(cl.xyz, cl.T, [((cl.feat,), [0, 1, 2]), (cl.rgb, [3])])
+        g.fuse_pointcloud(cuda_xyz(cl), cl.T, [(feat_t, [0, 1, 2]), (torch.from_numpy(cl.rgb).cuda(), [3])])
+        compare_states(gpu_state(g), o, what=f"bf16 scan {k}", bf16_rel=2.0 ** -7)
