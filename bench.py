@@ -1,0 +1,544 @@
+#!/usr/bin/env python
+"""Throughput of the multi-modal map update on GB300.
+
+Default workload (one step = one robot pose): move the 500 x 500 map (0.04 m cells) to the
+robot, then fuse one multi-modal cloud = 128-beam LiDAR (128 x 2048 rays) + 640 x 480 depth
+camera (569,344 points, misses kept as NaN) with per-point RGB and 20-class probabilities,
+into height + colour average + Dirichlet classes + class max + exponential average layers.
+Ten poses along a seeded path are cycled. Headline: points fused per second.
+
+Also reported on the same line: end-to-end throughput through the public API with host
+buffers, the dominant kernel's roofline, per-kernel times, the CPU oracle on the host cores,
+the batched path (512 maps of 200 x 200, RGB + 16-d BF16 features, one call) against 512
+plain per-map calls, and image fusion (4 cameras of 848 x 480, 64-d features + 20 classes).
+
+python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "points fused/sec & map updates/sec (plain vs batched BF16), % of HBM peak"
+UNIT = "points/s"
+WORKLOAD = ("multi-modal point clouds: 128-beam LiDAR (128x2048 rays, 0.5-40 m) + 640x480 depth "
+            "camera per pose, RGB + 20-class probabilities per point, 10-pose seeded path; map "
+            "500x500 at 0.04 m; layers: height (Kalman + gate), colour average, Dirichlet classes, "
+            "class max, exponential average; one step = move + fuse one pose")
+FLUSH_BYTES = 512 << 20  # > 129 MB L2
+
+
+def multimodal_layer_specs(M):
+    return [M.Layer(3, M.LATEST), M.Layer(20, M.DIRICHLET, alpha0=1.0), M.Layer(20, M.CLASSMAX),
+            M.Layer(20, M.EXPAVG, w=0.1)]
+
+
+def cell_bytes(layers, M):
+    """Algorithmic bytes read + written per touched cell by one point fuse."""
+    b = 8 + 8 + 8 + 8 + 8  # h, var, flags, n_acc, n_rej: read + write
+    for L in layers:
+        es = 4 if L.dtype == M.F32 else 2
+        if L.rule == M.LATEST:
+            b += es * L.channels                    # write
+        elif L.rule in (M.EXPAVG, M.DIRICHLET):
+            b += 2 * es * L.channels                # read + write
+        elif L.rule == M.GAUSS:
+            b += 2 * es * L.channels + 8            # read + write, variance read + write
+        elif L.rule == M.CLASSMAX:
+            b += 8                                  # write id + confidence
+    return b
+
+
+# ----------------------------------------------------------------------------- environment
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.idx), "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if len(r) > 5 + k and r[5 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2309_16818_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:12]
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if that summary was
+    taken from the current kernel sources; else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.md")
+    if not os.path.exists(p):
+        return None
+    src = kernel_source_hash()
+    for line in open(p):
+        m = re.match(r"\|\s*(\w+)\s*\|\s*([0-9a-f]{12})\s*\|\s*([0-9.eE+]+)\s*\|", line)
+        if m and m.group(1) == kernel and m.group(2) == src:
+            return float(m.group(3))
+    return None
+
+
+# ----------------------------------------------------------------------------- distributed
+
+def dist_setup():
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    return rank, ws, local
+
+
+def barrier(ws):
+    import torch
+    torch.cuda.synchronize()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------- our arm
+
+def run_ours(args):
+    import torch
+    from paper_2309_16818_gb300 import mem as M
+    from paper_2309_16818_gb300 import synth
+
+    rank, ws, local = dist_setup()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    c = synth.config2(seed=rank, n_poses=10)
+    W, res = c["W"], c["res"]
+    layers = multimodal_layer_specs(M)
+    n_pose = len(c["scans"])
+    xyz = [torch.from_numpy(s.xyz).to(dev) for s in c["scans"]]
+    rgb = [torch.from_numpy(s.rgb).to(dev) for s in c["scans"]]
+    prb = [torch.from_numpy(s.probs).to(dev) for s in c["scans"]]
+    npts = [s.n for s in c["scans"]]
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    m = M.Map(W, res, layers, max_points=max(npts) + 1024)
+    stream = torch.cuda.current_stream()
+
+    def step(k):
+        m.move(c["poses"][k][:2])
+        m.fuse_pointcloud(xyz[k], c["scans"][k].T, [(rgb[k], [0]), (prb[k], [1, 2, 3])])
+
+    # per-pose statistics (untimed): kept points and touched cells
+    stats = []
+    for k in range(n_pose):
+        step(k)
+        stats.append(m.get_stats())
+    m.check()
+
+    for i in range(args.warmup):
+        step(i % n_pose)
+    barrier(ws)
+    m.set_profiling(True)
+    m.get_profile()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    pts = 0
+    with ClockSampler(local) as clk:
+        barrier(ws)
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            k = (args.warmup + i) % n_pose
+            flush.fill_(i & 0xFF)            # evict the previous step from L2 (outside the events)
+            evs[i][0].record(stream)
+            step(k)
+            evs[i][1].record(stream)
+            pts += npts[k]
+        barrier(ws)
+        wall = time.perf_counter() - t0
+    m.check()
+    prof = m.get_profile()
+    m.set_profiling(False)
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    dev_s = sum(step_ms) / 1e3
+    dev_s_max = max_over_ranks(dev_s, ws)
+    total_pts = pts * ws
+    value = total_pts / dev_s_max
+
+    # ---- dominant kernel roofline
+    K = args.steps
+    mean = lambda key: float(np.mean([s[key] for s in stats]))
+    n_mean = float(np.mean(npts))
+    kept, cells = mean("kept"), mean("short_cells") + mean("long_cells")
+    P = stats[0]["passes"]
+    payload = 3 + 80
+    cb = cell_bytes(layers, M)
+    algo = {  # algorithmic bytes per launch
+        "key": n_mean * 16,
+        "radix_sort": n_mean * 16,
+        "segments": n_mean * 4 + cells * 8,
+        "fuse_small": None, "fuse_large": None,
+        "fuse": kept * (4 + 12 + payload) + cells * (cb + 12),
+        "move": None,
+    }
+    launches = {"key": K, "digit_scan": K, "radix_sort": K * P, "segments": K, "fuse_small": K,
+                "fuse_large": K, "move": prof["move"][1]}
+    kern = {}
+    for name, (ms, calls) in prof.items():
+        if calls:
+            kern[name] = {"ms_total": round(ms, 4), "launches": launches.get(name, calls),
+                          "us_per_launch": round(1e3 * ms / launches.get(name, calls), 3)}
+    fuse_ms = prof["fuse_small"][0] + prof["fuse_large"][0]
+    kern["fuse"] = {"ms_total": round(fuse_ms, 4), "launches": K, "us_per_launch": round(1e3 * fuse_ms / K, 3),
+                    "note": "fuse_small + fuse_large (one fused per-cell stage)"}
+    cand = {"key": prof["key"][0], "radix_sort": prof["radix_sort"][0], "segments": prof["segments"][0],
+            "fuse": fuse_ms}
+    dom = max(cand, key=cand.get)
+    per_launch_s = cand[dom] / 1e3 / launches.get(dom, K)
+    peak, peak_kind = peaks()
+    achieved = algo[dom] / per_launch_s / 1e9
+    ncu_name = {"fuse": "k_fuse_small", "radix_sort": "k_onesweep", "key": "k_points_key",
+                "segments": "k_segments"}[dom]
+    traffic = ncu_traffic(ncu_name)
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
+                "peak_kind": f"{peak_kind} (copy bandwidth)", "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "algorithmic_bytes_per_launch": round(algo[dom])}
+    # whole-step HBM fraction (all kernels of the step against the step's algorithmic bytes)
+    step_bytes = n_mean * 12 + kept * payload + cells * cb
+    step_frac = step_bytes / (dev_s / K) / 1e9 / peak
+
+    gpu_launches = int(sum(launches[k] for k in ("key", "digit_scan", "radix_sort", "segments",
+                                                   "fuse_small", "fuse_large")) + prof["move"][1])
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        hx = [torch.from_numpy(s.xyz).pin_memory() for s in c["scans"]]
+        hr = [torch.from_numpy(s.rgb).pin_memory() for s in c["scans"]]
+        hp = [torch.from_numpy(s.probs).pin_memory() for s in c["scans"]]
+        nmax = max(npts)
+        dx = torch.empty((nmax, 3), dtype=torch.float32, device=dev)
+        dr = torch.empty((nmax, 3), dtype=torch.uint8, device=dev)
+        dp = torch.empty((nmax, 20), dtype=torch.float32, device=dev)
+        hh = torch.empty(W * W, dtype=torch.float32).pin_memory()
+        dh = torch.empty(W * W, dtype=torch.float32, device=dev)
+        eev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        h2d = d2h = 0
+        for i in range(args.warmup + K):
+            k = i % n_pose
+            n = npts[k]
+            if i >= args.warmup:
+                flush.fill_(i & 0xFF)
+                eev[i - args.warmup][0].record(stream)
+            dx[:n].copy_(hx[k], non_blocking=True)
+            dr[:n].copy_(hr[k], non_blocking=True)
+            dp[:n].copy_(hp[k], non_blocking=True)
+            m.move(c["poses"][k][:2])
+            m.fuse_pointcloud(dx[:n], c["scans"][k].T, [(dr[:n], [0]), (dp[:n], [1, 2, 3])])
+            m.get_layer(M.LAYER_HEIGHT, out=dh)
+            hh.copy_(dh, non_blocking=True)
+            if i >= args.warmup:
+                eev[i - args.warmup][1].record(stream)
+                h2d += n * (12 + 3 + 80)
+                d2h += W * W * 4
+        torch.cuda.synchronize()
+        e_s = max_over_ranks(sum(a.elapsed_time(b) for a, b in eev) / 1e3, ws)
+        e_pts = ws * sum(npts[i % n_pose] for i in range(args.warmup, args.warmup + K))
+        e2e = {"value": round(e_pts / e_s, 1), "unit": UNIT, "h2d_bytes_per_step": int(h2d / K),
+               "d2h_bytes_per_step": int(d2h / K),
+               "note": "pinned host cloud -> device, move + fuse, height layer -> pinned host"}
+
+    extra = {}
+    if not args.no_batched:
+        extra["batched"] = bench_batched(args, dev, flush, ws)
+    if not args.no_image:
+        extra["image"] = bench_image(args, dev, flush, ws, c)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline(c, budget_s=args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": ws, "steps": K,
+            "warmup": args.warmup, "ms_per_step": round(1e3 * dev_s_max / K, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded terrain, ray-cast LiDAR + depth camera; stands in for the paper's ZED/VLP-16/depth clouds)",
+            "config": {"workload": WORKLOAD, "points_per_step": round(n_mean), "kept_points_per_step": round(kept),
+                       "touched_cells_per_step": round(cells), "map": "500x500 @ 0.04 m",
+                       "radix_passes": P, "l2": "512 MiB write between timed steps, outside the per-step events",
+                       "parallelism": f"replicas x{ws} (one independent map per GPU)"},
+            "map_updates_per_s": round(ws * K / dev_s_max, 2),
+            "hbm_frac_step": round(step_frac, 4),
+            "roofline": roofline, "kernels": kern, "gpu_launches": gpu_launches,
+            "wall_s": round(wall, 3), "clocks": clk.summary(), "e2e": e2e,
+            "cpu_baseline": cpu, "extra": extra,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def bench_batched(args, dev, flush, ws):
+    """512 independent 200 x 200 maps (RGB + 16-d BF16 Gaussian features) fused in one
+    graph-replayed call vs 512 plain per-map calls; map updates per second."""
+    import torch
+    from paper_2309_16818_gb300 import mem as M
+    from paper_2309_16818_gb300 import synth
+    c = synth.config4(n_maps=args.batch_maps)
+    B, W, res = len(c["clouds"]), c["W"], c["res"]
+    layers = [M.Layer(3, M.LATEST), M.Layer(16, M.GAUSS, dtype=M.BF16, var_meas=1.0)]
+    xyz, rgb, feat, _, T = synth.concat_clouds(c["clouds"])
+    n = int(c["offsets"][-1])
+    dx = torch.from_numpy(xyz).to(dev)
+    dr = torch.from_numpy(rgb).to(dev)
+    df = torch.from_numpy(feat.view(np.int16)).to(dev).view(torch.bfloat16)
+    srcs = [(dr, [0]), (df, [1])]
+    stream = torch.cuda.current_stream()
+    mb = M.Map(W, res, layers, n_maps=B, max_points=n + 4096)
+    reps = max(3, args.steps // 4)
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        evs = []
+        for i in range(reps):
+            flush.fill_(i)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            evs.append((a, b))
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in evs) / 1e3 / reps
+
+    t_batch = timed(lambda: mb.fuse_pointcloud_batch(c["offsets"], dx, T, srcs))
+    mb.check()
+    prof_b = None
+    mb.set_profiling(True)
+    mb.fuse_pointcloud_batch(c["offsets"], dx, T, srcs)
+    prof_b = {k: round(v[0], 4) for k, v in mb.get_profile().items() if v[1]}
+    st = mb.get_stats()
+    mb.set_profiling(False)
+    del mb
+    plain = [M.Map(W, res, layers, max_points=cl.n + 1024) for cl in c["clouds"]]
+    off = c["offsets"]
+
+    def run_plain():
+        for b, cl in enumerate(c["clouds"]):
+            s, e = int(off[b]), int(off[b + 1])
+            plain[b].fuse_pointcloud(dx[s:e], cl.T, [(dr[s:e], [0]), (df[s:e], [1])])
+
+    t_plain = timed(run_plain)
+    for p in plain:
+        p.close()
+    t_batch = max_over_ranks(t_batch, ws)
+    t_plain = max_over_ranks(t_plain, ws)
+    peak, _ = peaks()
+    cb = cell_bytes(layers, M)
+    cells = st["short_cells"] + st["long_cells"]
+    algo = n * 12 + st["kept"] * (3 + 32) + cells * cb
+    return {"workload": f"{B} maps 200x200 @ 0.05 m, {n} points (log-uniform 5k-60k per map), RGB avg + 16-d BF16 Gaussian features",
+            "batched_map_updates_per_s": round(ws * B / t_batch, 1),
+            "plain_map_updates_per_s": round(ws * B / t_plain, 1),
+            "batched_points_per_s": round(ws * n / t_batch, 1),
+            "speedup": round(t_plain / t_batch, 3), "ms_batched": round(1e3 * t_batch, 4),
+            "ms_plain_512_calls": round(1e3 * t_plain, 4), "hbm_frac": round(algo / t_batch / 1e9 / peak, 4),
+            "kernels_ms": prof_b}
+
+
+def bench_image(args, dev, flush, ws, c2):
+    """4 cameras 848 x 480 (64-d F32 features + 20-class segmentation) fused into the
+    500 x 500 map pre-filled by one pose; cells per second."""
+    import torch
+    from paper_2309_16818_gb300 import mem as M
+    from paper_2309_16818_gb300 import synth
+    layers = [M.Layer(64, M.GAUSS, var_meas=1.0), M.Layer(20, M.DIRICHLET), M.Layer(20, M.CLASSMAX),
+              M.Layer(64, M.GAUSS, dtype=M.BF16, var_meas=1.0)]
+    cams = synth.cameras_around(3, c2["poses"][0], c2["terrain"])
+    m = M.Map(c2["W"], c2["res"], layers)
+    s = c2["scans"][0]
+    m.move(c2["poses"][0][:2])
+    m.fuse_pointcloud(torch.from_numpy(s.xyz).to(dev), s.T)
+    imgs = [(torch.from_numpy(cam.feat).to(dev), torch.from_numpy(cam.seg).to(dev)) for cam in cams]
+    stream = torch.cuda.current_stream()
+    vis = torch.empty(c2["W"] ** 2, dtype=torch.uint8, device=dev)
+
+    def one():
+        for cam, (f, sg) in zip(cams, imgs):
+            m.fuse_image(cam.H, cam.Wi, cam.K, cam.T, [(f, [0, 3]), (sg, [1, 2])], vis=vis)
+
+    for _ in range(2):
+        one()
+    reps = max(3, args.steps // 4)
+    tot = 0.0
+    for i in range(reps):
+        flush.fill_(i)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        one()
+        b.record(stream)
+        torch.cuda.synchronize()
+        tot += a.elapsed_time(b) / 1e3
+    m.check()
+    t = max_over_ranks(tot / reps, ws)
+    nvis = int(vis.sum().item())
+    return {"workload": "4 cameras 848x480, 64-d F32 + 64-d BF16 Gaussian features, 20-class Dirichlet + class max, 500x500 map",
+            "ms_per_4_cameras": round(1e3 * t, 4), "camera_fuses_per_s": round(ws * 4 / t, 1),
+            "cells_per_s": round(ws * 4 * c2["W"] ** 2 / t, 1), "visible_cells_last_camera": nvis}
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+
+def oracle_step_fn(c):
+    import oracle as O
+    layers = [O.Layer(3, O.LATEST), O.Layer(20, O.DIRICHLET, alpha0=1.0), O.Layer(20, O.CLASSMAX),
+              O.Layer(20, O.EXPAVG, w=0.1)]
+    o = O.OracleMap(O.Params(W=c["W"], res=c["res"], layers=layers))
+
+    def step(k):
+        s = c["scans"][k]
+        o.move(c["poses"][k][:2])
+        o.fuse_points(s.xyz, s.T, [(s.rgb, [0]), (s.probs, [1, 2, 3])])
+        return s.n
+    return step
+
+
+def cpu_baseline(c, budget_s=15.0):
+    step = oracle_step_fn(c)
+    t0 = time.perf_counter()
+    pts = 0
+    k = 0
+    while time.perf_counter() - t0 < budget_s and k < 200:
+        pts += step(k % len(c["scans"]))
+        k += 1
+    dt = time.perf_counter() - t0
+    return {"value": round(pts / dt, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{k} full poses of the same workload (move + fuse), single-threaded C oracle, "
+                      f"{dt:.1f} s on {len(os.sched_getaffinity(0))} available host cores"}
+
+
+def run_reference(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2309_16818_gb300 import synth
+    c = synth.config2(seed=0, n_poses=10)
+    step = oracle_step_fn(c)
+    for i in range(args.warmup):
+        step(i % 10)
+    t0 = time.perf_counter()
+    pts = 0
+    for i in range(args.steps):
+        pts += step((args.warmup + i) % 10)
+    dt = time.perf_counter() - t0
+    v = pts / dt
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(v, 1), "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * dt / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "parallelism": "rank 0 only (CPU)"},
+        "cpu_baseline": {"value": round(v, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} full poses, single-threaded C oracle"},
+        "e2e": {"value": round(v, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-image", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--batch-maps", type=int, default=512)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        from paper_2309_16818_gb300 import build
+        if not os.path.exists(os.path.join(ROOT, "paper_2309_16818_gb300", "libmem.so")):
+            build.build()
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()
