@@ -215,6 +215,35 @@ mem_status mem_get_profile(mem_map *m, double ms[MEM_PROFILE_SLOTS], int64_t cal
 /* Synchronise `stream`; out = {short cells, long cells, kept points, radix
  * passes} of the last point fuse (host output). */
 mem_status mem_get_stats(mem_map *m, void *stream, int64_t out[4]);
+
+/* Allocation-free height fuse. The paper has no counterpart: this entry point
+ * exists for callers that cannot call cudaMalloc -- code that runs inside
+ * another framework's memory pool, real-time loops that forbid allocation
+ * after start-up, hosts whose device allocator is owned by someone else.
+ * It fuses one point cloud into caller-owned height layers (the height update
+ * with outlier gate of mem_fuse_pointcloud, no multi-modal layers) and
+ * allocates nothing: no cudaMalloc, cudaFree, pinned memory or allocating
+ * library routine. Its sort and segment scratch is one file-scope device
+ * array sized for MEM_NOALLOC_MAX_POINTS points (about 9.5 MB, held by every
+ * GPU that loads the library until the process exits).
+ *   cfg       host; n_maps must be 1 and n_layers 0; max_points is ignored
+ *   origin_xy host; world xy of the map centre (cell W/2 lower corner)
+ *   n         points, 0 <= n <= MEM_NOALLOC_MAX_POINTS (larger: MEM_ERR_ARG)
+ *   xyz       device float32 [n][3], sensor frame
+ *   h, var    device float32 [W*W] elevation and variance (cell iy*W + ix)
+ *   valid     device uint32 [W*W], 1 once the cell holds a height, else 0
+ *   n_acc, n_rej device uint32 [W*W] cumulative accepted / rejected points
+ * The caller initialises the layers (all zero = empty map). The first call on
+ * a device looks up the array's device address (cudaGetSymbolAddress) and
+ * sets kernel attributes; make that first call before any stream capture.
+ * Every call shares the one array and overwrites it: calls that overlap on
+ * the GPU (other streams, other threads) race and must be serialised by the
+ * caller. */
+#define MEM_NOALLOC_MAX_POINTS (1 << 18)
+mem_status mem_fuse_pointcloud_noalloc(const mem_map_config *cfg, const double origin_xy[2],
+                                       int64_t n, const float *xyz, const double T_map_sensor[16],
+                                       float *h, float *var, uint32_t *valid, uint32_t *n_acc,
+                                       uint32_t *n_rej, void *stream);
 /* Thread-local description of the last error. */
 const char *mem_last_error(void);
 

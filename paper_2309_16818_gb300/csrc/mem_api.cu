@@ -49,6 +49,19 @@ size_t dtype_size(int dt) {
 }
 }  // namespace
 
+namespace memh {
+mem_status api_fail(mem_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+mem_status api_cuda_fail(cudaError_t e, const char* what) { return cuda_fail(e, what); }
+}  // namespace memh
+
 // ---------------------------------------------------------------------------
 // device kernels: reset of cells, layer copies
 

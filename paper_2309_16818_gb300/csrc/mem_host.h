@@ -80,5 +80,7 @@ cudaError_t alloc_scratch(Map* m, int64_t cap);
 void free_scratch(Map* m);
 int key_bits_for(const Map* m);
 cudaError_t prepare_kernels();
+mem_status api_fail(mem_status s, const char* fmt, ...);
+mem_status api_cuda_fail(cudaError_t e, const char* what);
 
 }  // namespace memh

@@ -26,7 +26,8 @@ PART_VALUE, PART_THETA, PART_VAR, PART_OBSERVED = range(4)
 EXPORTS = ["mem_create_map", "mem_destroy_map", "mem_move_map", "mem_fuse_pointcloud",
            "mem_fuse_pointcloud_batch", "mem_fuse_image", "mem_get_layer", "mem_set_layer",
            "mem_get_origin", "mem_check", "mem_last_error", "mem_set_tuning", "mem_get_tuning",
-           "mem_set_profiling", "mem_get_profile", "mem_get_stats"]
+           "mem_set_profiling", "mem_get_profile", "mem_get_stats", "mem_fuse_pointcloud_noalloc"]
+NOALLOC_MAX_POINTS = 1 << 18
 PROFILE_SLOTS = ["key", "digit_scan", "radix_sort", "segments", "fuse_small", "fuse_large",
                  "time_var", "image", "move"]
 
@@ -77,6 +78,7 @@ def lib():
             "mem_get_origin": [P, I32, P], "mem_check": [P, P], "mem_last_error": [],
             "mem_set_tuning": [P, I32, I32, I32], "mem_get_tuning": [P, P],
             "mem_set_profiling": [P, I32], "mem_get_profile": [P, P, P], "mem_get_stats": [P, P, P],
+            "mem_fuse_pointcloud_noalloc": [P, P, I64, P, P, P, P, P, P, P, P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -113,6 +115,28 @@ def _stream(stream):
 def _pose(T, n=1):
     a = np.ascontiguousarray(np.asarray(T, dtype=np.float64).reshape(n * 16))
     return a
+
+
+def fuse_pointcloud_noalloc(W, res, xyz, T, h, var, valid, n_acc, n_rej, origin=(0.0, 0.0),
+                            stream=None, **params):
+    """Allocation-free height fuse into caller-owned tensors (mem_fuse_pointcloud_noalloc):
+    h, var float32 [W*W]; valid, n_acc, n_rej int32 [W*W] (uint32 bit patterns)."""
+    cfg = MapConfig()
+    cfg.W, cfg.n_maps, cfg.res, cfg.n_layers = W, 1, res, 0
+    d = dict(sigma0=0.01, sigma1=0.002, gate_lambda=2.0, outlier_var=0.0, time_var=0.0,
+             range_min=0.1, range_max=50.0, z_near=0.05)
+    d.update(params)
+    for k, v in d.items():
+        setattr(cfg, k, v)
+    o = np.ascontiguousarray(origin, dtype=np.float64)
+    n = int(xyz.shape[0])
+    for t in (h, var, valid, n_acc, n_rej):
+        assert t.is_cuda and t.is_contiguous() and t.numel() == W * W and t.element_size() == 4
+    _ck(lib().mem_fuse_pointcloud_noalloc(C.byref(cfg), o.ctypes.data, n,
+                                          C.c_void_p(xyz.data_ptr() if n else 0), _pose(T).ctypes.data,
+                                          C.c_void_p(h.data_ptr()), C.c_void_p(var.data_ptr()),
+                                          C.c_void_p(valid.data_ptr()), C.c_void_p(n_acc.data_ptr()),
+                                          C.c_void_p(n_rej.data_ptr()), _stream(stream)))
 
 
 @dataclass
