@@ -194,13 +194,12 @@ mem_status mem_get_origin(const mem_map *m, int32_t map_index, double out_xy[2])
 /* Synchronise `stream` and report (then clear) the map's device error word. */
 mem_status mem_check(mem_map *m, void *stream);
 
-/* Schedule of the point path (no effect on results beyond the float32
- * summation order inside a cell): radix_bits in [8, 10] is the digit width
- * of the key sort; cells with at most small_max points are fused by one
- * thread, longer runs by one warp; blocks_per_sm sizes the persistent grids.
- * Synchronises the device. */
-mem_status mem_set_tuning(mem_map *m, int32_t radix_bits, int32_t small_max, int32_t blocks_per_sm);
-/* out = {radix_bits, small_max, blocks_per_sm, radix passes} (host). */
+/* Schedule of the point path (no effect on the results): radix_bits in
+ * [8, 10] is the digit width of the key sort (at most 4 passes);
+ * blocks_per_sm in [1, 32] sizes the persistent grids. Synchronises the
+ * device. */
+mem_status mem_set_tuning(mem_map *m, int32_t radix_bits, int32_t blocks_per_sm);
+/* out = {radix_bits, blocks_per_sm, radix passes, 0} (host). */
 mem_status mem_get_tuning(const mem_map *m, int32_t out[4]);
 
 /* Per-kernel timing: with profiling on, every launch group of this map is
@@ -212,8 +211,9 @@ mem_status mem_get_tuning(const mem_map *m, int32_t out[4]);
 #define MEM_PROFILE_SLOTS 16
 mem_status mem_set_profiling(mem_map *m, int32_t on);
 mem_status mem_get_profile(mem_map *m, double ms[MEM_PROFILE_SLOTS], int64_t calls[MEM_PROFILE_SLOTS]);
-/* Synchronise `stream`; out = {short cells, long cells, kept points, radix
- * passes} of the last point fuse (host output). */
+/* Synchronise `stream`; out = {cells whose points cross a 32-point window of
+ * the sorted order, touched cells, kept points, radix passes} of the last
+ * point fuse (host output). */
 mem_status mem_get_stats(mem_map *m, void *stream, int64_t out[4]);
 
 /* Allocation-free height fuse. The paper has no counterpart: this entry point

@@ -67,38 +67,41 @@ mem_status api_cuda_fail(cudaError_t e, const char* what) { return cuda_fail(e, 
 
 namespace memk {
 
+// A cell is reset by clearing its flags (height invalid, no layer observed)
+// and its counters: every kernel treats the stored values of an unobserved
+// layer (and the height of an invalid cell) as the layer's initial value.
 __device__ __forceinline__ void reset_cell(const MapDev& md, int64_t g) {
-  md.h[g] = 0.f;
-  md.var[g] = 0.f;
   md.flags[g] = 0u;
   md.n_acc[g] = 0u;
   md.n_rej[g] = 0u;
-  for (int l = 0; l < md.n_layers; ++l) {
-    const LayerDev& L = md.L[l];
-    for (int k = 0; k < L.S; ++k) {
-      float v = 0.f;
-      if (L.rule == MEM_RULE_DIRICHLET) v = L.alpha0;
-      if (L.rule == MEM_RULE_CLASSMAX && k == 0) v = -1.f;
-      st_layer(L, g * L.S + k, v);
-    }
-    if (L.gvar) L.gvar[g] = 0.f;
-  }
 }
 
 // Reset every cell of every map (map < 0), or the cells of `map` that entered
 // with the shift (sx, sy): new logical (ix, iy) had no old cell
 // (ix + sx, iy + sy) inside the map.
 __global__ void k_reset(MapDev md, int map, int sx, int sy, int rx, int ry) {
-  const int64_t total = map < 0 ? (int64_t)md.n_maps * md.W2 : (int64_t)md.W2;
-  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < total;
-       c += (int64_t)gridDim.x * blockDim.x) {
-    if (map < 0) {
+  if (map < 0) {
+    const int64_t total = (int64_t)md.n_maps * md.W2;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < total;
+         c += (int64_t)gridDim.x * blockDim.x)
       reset_cell(md, c);
-      continue;
+    return;
+  }
+  // only the entering strips: |sx| columns and |sy| rows (corners twice)
+  const u32 W = (u32)md.W;
+  const u32 ax = (u32)min(abs(sx), md.W), ay = (u32)min(abs(sy), md.W);
+  const u32 total = (ax + ay) * W;
+  for (u32 u = blockIdx.x * blockDim.x + threadIdx.x; u < total; u += gridDim.x * blockDim.x) {
+    int ix, iy;
+    if (u < ax * W) {
+      const u32 col = u / W;
+      iy = (int)(u - col * W);
+      ix = sx > 0 ? (int)(W - 1 - col) : (int)col;
+    } else {
+      const u32 v = u - ax * W, row = v / W;
+      ix = (int)(v - row * W);
+      iy = sy > 0 ? (int)(W - 1 - row) : (int)row;
     }
-    const int ix = (int)(c % md.W), iy = (int)(c / md.W);
-    const int ox = ix + sx, oy = iy + sy;
-    if (ox >= 0 && ox < md.W && oy >= 0 && oy < md.W) continue;
     int px = ix + rx;
     if (px >= md.W) px -= md.W;
     int py = iy + ry;
@@ -123,11 +126,11 @@ __global__ void k_layer_copy(MapDev md, int map, int rx, int ry, int layer, int 
       switch (layer) {
         case MEM_LAYER_HEIGHT:
           if (to_map) md.h[g] = ((const float*)buf)[j];
-          else ((float*)buf)[j] = md.h[g];
+          else ((float*)buf)[j] = (md.flags[g] & kFlagValid) ? md.h[g] : 0.f;
           break;
         case MEM_LAYER_VARIANCE:
           if (to_map) md.var[g] = ((const float*)buf)[j];
-          else ((float*)buf)[j] = md.var[g];
+          else ((float*)buf)[j] = (md.flags[g] & kFlagValid) ? md.var[g] : 0.f;
           break;
         case MEM_LAYER_VALID:
           if (to_map) md.flags[g] = (md.flags[g] & ~kFlagValid) | (((const uint8_t*)buf)[j] ? 1u : 0u);
@@ -145,6 +148,24 @@ __global__ void k_layer_copy(MapDev md, int map, int rx, int ry, int layer, int 
       continue;
     }
     const LayerDev& L = md.L[layer];
+    const bool obs = md.flags[g] & (2u << layer);
+    if (!to_map && !obs) {  // an unobserved cell reads as the layer's initial state
+      if (part == MEM_PART_VALUE) {
+        if (L.dtype == MEM_F32)
+          for (int k = 0; k < L.S; ++k) ((float*)buf)[j * L.S + k] = layer_init(L, k);
+        else if (L.dtype == MEM_BF16)
+          for (int k = 0; k < L.S; ++k) ((__nv_bfloat16*)buf)[j * L.S + k] = __float2bfloat16_rn(layer_init(L, k));
+        else
+          for (int k = 0; k < L.S; ++k) ((__half*)buf)[j * L.S + k] = __float2half_rn(layer_init(L, k));
+      } else if (part == MEM_PART_THETA) {
+        for (int k = 0; k < L.S; ++k) ((float*)buf)[j * L.S + k] = __frcp_rn((float)L.S);
+      } else if (part == MEM_PART_VAR) {
+        ((float*)buf)[j] = 0.f;
+      } else {
+        ((uint8_t*)buf)[j] = 0;
+      }
+      continue;
+    }
     switch (part) {
       case MEM_PART_VALUE: {
         if (L.dtype == MEM_F32) {
@@ -222,11 +243,40 @@ cudaError_t alloc_scratch(Map* m, int64_t cap) {
   A(vals0, u32, cap + 4);
   A(vals1, u32, cap + 4);
   A(lookback, u32, 4 * tiles * 1024);
-  A(seg_small, uint2, cap);
-  A(seg_large, uint2, cap);
 #undef A
   md.cap = cap;
   md.cap_tiles = tiles;
+  md.partial = nullptr;
+  md.partial_cap = 0;
+  return cudaSuccess;
+}
+
+// partial records of window-crossing runs: 2 per 32-point window, acc floats each
+static cudaError_t ensure_partial(Map* m, int acc) {
+  MapDev& md = m->md;
+  const int64_t need = 2 * (md.cap / 32 + 2) * (int64_t)acc;
+  if (need <= md.partial_cap) return cudaSuccess;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return e;
+  if (md.partial) {
+    for (auto it = m->scratch_allocs.begin(); it != m->scratch_allocs.end(); ++it)
+      if (*it == md.partial) {
+        m->scratch_allocs.erase(it);
+        break;
+      }
+    cudaFree(md.partial);
+    md.partial = nullptr;
+    md.partial_cap = 0;
+  }
+  void* p;
+  e = dalloc(m, &p, sizeof(float) * (size_t)need, true);
+  if (e != cudaSuccess) return e;
+  md.partial = (float*)p;
+  md.partial_cap = need;
+  if (m->graph) {  // the graph captured the old buffer
+    cudaGraphExecDestroy(m->graph);
+    m->graph = nullptr;
+  }
   return cudaSuccess;
 }
 
@@ -368,7 +418,7 @@ extern "C" mem_status mem_create_map(const mem_map_config* cfg, mem_map** out) {
   ALLOC(md.n_rej, uint32_t, cells, "alloc n_rej");
   for (int l = 0; l < cfg->n_layers; ++l) {
     const mem_layer_desc& D = cfg->layers[l];
-    LayerDev& L = md.L[l];
+    LayerDev& L = m->Lh[l];
     L.C = D.channels;
     L.S = D.rule == MEM_RULE_CLASSMAX ? 2 : D.channels;
     L.dtype = D.dtype;
@@ -384,6 +434,14 @@ extern "C" mem_status mem_create_map(const mem_map_config* cfg, mem_map** out) {
     if (D.rule == MEM_RULE_GAUSS) {
       ALLOC(L.gvar, float, cells, "alloc gauss variance");
     }
+  }
+  {
+    LayerDev* dl = nullptr;
+    ALLOC(dl, LayerDev, cfg->n_layers > 0 ? cfg->n_layers : 1, "alloc layer table");
+    if (cfg->n_layers > 0 &&
+        (e = cudaMemcpy(dl, m->Lh, sizeof(LayerDev) * cfg->n_layers, cudaMemcpyHostToDevice)) != cudaSuccess)
+      return bail(e, "upload layer table");
+    md.L = dl;
   }
   ALLOC(md.hist, uint32_t, 4 * 1024 + 16, "alloc hist");
   md.counters = md.hist + 4 * 1024;
@@ -430,16 +488,14 @@ extern "C" mem_status mem_destroy_map(mem_map* mm) {
   return MEM_OK;
 }
 
-extern "C" mem_status mem_set_tuning(mem_map* mm, int32_t radix_bits, int32_t small_max,
-                                     int32_t blocks_per_sm) {
+extern "C" mem_status mem_set_tuning(mem_map* mm, int32_t radix_bits, int32_t blocks_per_sm) {
   if (!mm) return fail(MEM_ERR_ARG, "map is NULL");
   if (radix_bits < 8 || radix_bits > 10) return fail(MEM_ERR_ARG, "radix_bits in [8, 10]");
-  if (small_max < 1 || small_max > 1024) return fail(MEM_ERR_ARG, "small_max in [1, 1024]");
   if (blocks_per_sm < 1 || blocks_per_sm > 32) return fail(MEM_ERR_ARG, "blocks_per_sm in [1, 32]");
   Map* m = &mm->m;
+  if ((m->key_bits + radix_bits - 1) / radix_bits > 4) return fail(MEM_ERR_ARG, "too many radix passes");
   cudaDeviceSynchronize();
   m->tune.radix_bits = radix_bits;
-  m->tune.small_max = small_max;
   m->tune.blocks_per_sm = blocks_per_sm;
   m->passes = (m->key_bits + radix_bits - 1) / radix_bits;
   if (m->passes > 4) return fail(MEM_ERR_ARG, "too many radix passes");
@@ -453,9 +509,9 @@ extern "C" mem_status mem_set_tuning(mem_map* mm, int32_t radix_bits, int32_t sm
 extern "C" mem_status mem_get_tuning(const mem_map* mm, int32_t out[4]) {
   if (!mm || !out) return fail(MEM_ERR_ARG, "NULL argument");
   out[0] = mm->m.tune.radix_bits;
-  out[1] = mm->m.tune.small_max;
-  out[2] = mm->m.tune.blocks_per_sm;
-  out[3] = mm->m.passes;
+  out[1] = mm->m.tune.blocks_per_sm;
+  out[2] = mm->m.passes;
+  out[3] = 0;
   return MEM_OK;
 }
 
@@ -507,6 +563,9 @@ static mem_status check_sources(const Map* m, int32_t n_sources, const mem_sourc
     out[q].C = s.channels;
     out[q].n_layers = s.n_layers;
     out[q].vec_ok = ((uintptr_t)s.data & 15) == 0;
+    out[q].has_classmax = 0;
+    for (int b = 0; b < s.n_layers; ++b)
+      if (m->cfg.layers[s.layers[b]].rule == MEM_RULE_CLASSMAX) out[q].has_classmax = 1;
     for (int b = 0; b < MEM_MAX_SOURCE_LAYERS; ++b) out[q].layers[b] = b < s.n_layers ? s.layers[b] : 0;
   }
   (void)image;
@@ -538,7 +597,17 @@ static mem_status run_points(Map* m, int nm, const int64_t* offsets, int64_t n, 
   job->xyz = xyz;
   job->n_maps = nm;
   job->n_src = n_src;
-  for (int q = 0; q < n_src; ++q) job->src[q] = src[q];
+  int acc = 8;  // record header
+  for (int q = 0; q < n_src; ++q) {
+    job->src[q] = src[q];
+    job->src[q].acc_off = acc;
+    acc += src[q].C + 2 * src[q].has_classmax;  // channel sums, then (max value, class)
+  }
+  job->acc = acc;
+  {
+    cudaError_t e = ensure_partial(m, acc);
+    if (e != cudaSuccess) return cuda_fail(e, "partial-record buffer");
+  }
   job->maps = (const MapCall*)(m->d_job + sizeof(PointJob));
   job->offsets = nm > 1 ? (const int64_t*)(m->d_job + sizeof(PointJob) + sizeof(MapCall) * nm) : nullptr;
   for (int b = 0; b < nm; ++b) {

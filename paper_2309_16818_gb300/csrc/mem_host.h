@@ -12,13 +12,13 @@ constexpr int kJobSlots = 8;
 
 struct Tuning {
   int radix_bits = 9;   // digit width of the radix sort (8..10)
-  int small_max = 8;    // segments up to this many points: one thread each
   int blocks_per_sm = 4;
 };
 
 struct Map {
   mem_map_config cfg;
   memk::MapDev md;
+  memk::LayerDev Lh[memk::kMaxLayers];  // host copy of the device layer table md.L
   Tuning tune;
   int passes = 1;
   int key_bits = 1;
@@ -51,7 +51,7 @@ struct Map {
 };
 
 // profile slots
-enum { kProfKey = 0, kProfDigits, kProfSort, kProfSegments, kProfFuseSmall, kProfFuseLarge,
+enum { kProfKey = 0, kProfDigits, kProfSort, kProfUnused, kProfFuseWindow, kProfFuseSpan,
        kProfTime, kProfImage, kProfMove, kProfSlots };
 
 // Brackets a launch group with events when profiling is on.

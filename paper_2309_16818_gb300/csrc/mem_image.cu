@@ -101,11 +101,11 @@ __device__ __forceinline__ void fuse_pixel_warp(const MapDev& md, const ImgParam
         }
       } else {
         const float s02 = (L.rule == MEM_RULE_GAUSS && obs) ? L.gvar[g] : 0.f;
-        for (int c = lane; c < s.C; c += 32)
-          apply_rule_ch(L, g, c, 1.f, ld_any(s.data, s.dtype, row + c), obs, s02);
+        const RuleCoef co = rule_coef(L, 1.f, 1.f, obs, s02);
+        for (int c = lane; c < s.C; c += 32) apply_rule(L, g * L.S + c, ld_any(s.data, s.dtype, row + c), co);
         if (L.rule == MEM_RULE_GAUSS) {
           __syncwarp();
-          if (lane == 0) L.gvar[g] = gauss_new_var(L, 1.f, obs, s02);
+          if (lane == 0) L.gvar[g] = co.var_new;
         }
       }
       __syncwarp();

@@ -38,7 +38,7 @@ struct MapDev {
   float res;
   float sigma0, sigma1, lam2, outlier_var, time_var, range_min, range_max, z_near;
   int n_layers;
-  LayerDev L[kMaxLayers];
+  const LayerDev* L;  // [n_layers] in device memory (indexed at run time by the kernels)
   float* h;
   float* var;
   u32* flags;  // bit0 valid, bit (1 + l) layer l observed
@@ -48,9 +48,9 @@ struct MapDev {
   u32 *keys0, *keys1, *vals0, *vals1;
   u32* hist;        // [passes][radix] digit counts, then exclusive offsets
   u32* lookback;    // [passes][tiles][radix]
-  u32* counters;    // [0..3] tile counters per pass, [4] n_small, [5] n_large
-  uint2* seg_small; // (start, end)
-  uint2* seg_large;
+  u32* counters;    // [0..3] tile counters per pass, [6] kept points
+  float* partial;   // [2 per 32-point window][acc] partial records of cells crossing windows
+  int64_t partial_cap;  // floats
   int* err;
   int64_t cap;      // point capacity of the scratch
   int64_t cap_tiles;
@@ -69,7 +69,9 @@ struct SrcDev {
   const void* data;
   int dtype, C, n_layers;
   int layers[kMaxSrcLayers];
-  int vec_ok;  // data is 16-byte aligned: rows may be read with vector loads
+  int vec_ok;        // data is 16-byte aligned: rows may be read with vector loads
+  int has_classmax;  // a CLASSMAX layer is bound: track the arg-max
+  int acc_off;       // offset of this source's sums (then maxima) in a partial record
 };
 
 // Per-call job of the point path, resident in device memory so the whole
@@ -81,6 +83,7 @@ struct PointJob {
   const MapCall* maps;     // [n_maps]
   int n_maps;
   int n_src;
+  int acc;  // floats per partial record: 8 header + per source C sums (+ max value, class)
   SrcDev src[kMaxSources];
 };
 
@@ -189,39 +192,68 @@ __device__ __forceinline__ void st_layer(const LayerDev& L, int64_t off, float v
   }
 }
 
-// Apply one rule to channel c of cell g from N observations with sum S
-// (and, for the Gaussian rule, the cell's prior variance s02; obs = observed).
-// CLASSMAX is handled by the callers (needs the whole row).
-__device__ __forceinline__ void apply_rule_ch(const LayerDev& L, int64_t g, int c, float N,
-                                              float S, bool obs, float s02) {
-  const int64_t off = g * L.S + c;
+// Per-(cell, layer) coefficients of a fusion rule for N observations, computed
+// once per cell so that each channel costs one multiply-add:
+//   LATEST    theta = S a                       (a = 1/N, Eq. 1)
+//   EXPAVG    theta = w (S a) + (1 - w) theta   (first observation: S a, Eq. 2)
+//   GAUSS     mu = a mu0 + b S with a = sf2/(N s02 + sf2), b = s02/(N s02 + sf2),
+//             var = sf2 s02/(N s02 + sf2)        (first observation: mu = S/N,
+//             var = sf2/N; Eqs. 6-7)
+//   DIRICHLET alpha = alpha + S                 (Eq. 12)
+struct RuleCoef {
+  float a, b, var_new;
+  bool obs;
+};
+
+__device__ __forceinline__ RuleCoef rule_coef(const LayerDev& L, float N, float rN, bool obs, float s02) {
+  RuleCoef r;
+  r.obs = obs;
+  r.a = rN;
+  r.b = 0.f;
+  r.var_new = 0.f;
+  if (L.rule == MEM_RULE_GAUSS) {
+    if (obs) {
+      const float rden = __frcp_rn(__fmaf_rn(N, s02, L.var_meas));
+      r.a = L.var_meas * rden;
+      r.b = s02 * rden;
+      r.var_new = L.var_meas * s02 * rden;
+    } else {
+      r.var_new = L.var_meas * rN;
+    }
+  }
+  return r;
+}
+
+// New value of one channel from its old value and the channel's sum S over
+// the cell's observations (not CLASSMAX, which needs the whole row).
+__device__ __forceinline__ float rule_value(const LayerDev& L, float old, float S, const RuleCoef& r) {
   switch (L.rule) {
-    case MEM_RULE_LATEST: st_layer(L, off, __fdiv_rn(S, N)); break;
+    case MEM_RULE_LATEST: return S * r.a;
     case MEM_RULE_EXPAVG: {
-      float a = __fdiv_rn(S, N);
-      float t = obs ? __fmaf_rn(L.w, a, __fmul_rn(L.one_minus_w, ld_layer(L, off))) : a;
-      st_layer(L, off, t);
-      break;
+      const float a = S * r.a;
+      return r.obs ? fmaf(L.w, a, L.one_minus_w * old) : a;
     }
-    case MEM_RULE_GAUSS: {
-      float mu;
-      if (obs) {
-        float den = __fmaf_rn(N, s02, L.var_meas);
-        mu = __fdiv_rn(__fmaf_rn(L.var_meas, ld_layer(L, off), __fmul_rn(s02, S)), den);
-      } else {
-        mu = __fdiv_rn(S, N);
-      }
-      st_layer(L, off, mu);
-      break;
-    }
-    case MEM_RULE_DIRICHLET: st_layer(L, off, __fadd_rn(ld_layer(L, off), S)); break;
-    default: break;
+    case MEM_RULE_GAUSS: return r.obs ? fmaf(r.a, old, r.b * S) : S * r.a;
+    case MEM_RULE_DIRICHLET: return (r.obs ? old : L.alpha0) + S;  // unobserved cell: prior alpha0
+    default: return old;
   }
 }
 
-__device__ __forceinline__ float gauss_new_var(const LayerDev& L, float N, bool obs, float s02) {
-  return obs ? __fdiv_rn(__fmul_rn(L.var_meas, s02), __fmaf_rn(N, s02, L.var_meas))
-             : __fdiv_rn(L.var_meas, N);
+// the stored value is only read for an observed cell: an unobserved cell
+// holds its layer's initial value whatever is in memory (lazy reset)
+__device__ __forceinline__ bool needs_old(const LayerDev& L, const RuleCoef& r) {
+  return r.obs && L.rule != MEM_RULE_LATEST;
+}
+
+__device__ __forceinline__ void apply_rule(const LayerDev& L, int64_t off, float S, const RuleCoef& r) {
+  st_layer(L, off, rule_value(L, needs_old(L, r) ? ld_layer(L, off) : 0.f, S, r));
+}
+
+// initial value of stored value k of a layer (what an unobserved cell holds)
+__device__ __forceinline__ float layer_init(const LayerDev& L, int k) {
+  if (L.rule == MEM_RULE_DIRICHLET) return L.alpha0;
+  if (L.rule == MEM_RULE_CLASSMAX && k == 0) return -1.f;
+  return 0.f;
 }
 
 // relaxed device-scope loads/stores for the radix-sort look-back

@@ -28,7 +28,7 @@ EXPORTS = ["mem_create_map", "mem_destroy_map", "mem_move_map", "mem_fuse_pointc
            "mem_get_origin", "mem_check", "mem_last_error", "mem_set_tuning", "mem_get_tuning",
            "mem_set_profiling", "mem_get_profile", "mem_get_stats", "mem_fuse_pointcloud_noalloc"]
 NOALLOC_MAX_POINTS = 1 << 18
-PROFILE_SLOTS = ["key", "digit_scan", "radix_sort", "segments", "fuse_small", "fuse_large",
+PROFILE_SLOTS = ["key", "digit_scan", "radix_sort", "segments", "fuse_window", "fuse_span",
                  "time_var", "image", "move"]
 
 
@@ -76,7 +76,7 @@ def lib():
             "mem_fuse_image": [P, I32, I32, I32, I32, P, P, P, P, P, P],
             "mem_get_layer": [P, I32, I32, I32, P, P], "mem_set_layer": [P, I32, I32, I32, P, P],
             "mem_get_origin": [P, I32, P], "mem_check": [P, P], "mem_last_error": [],
-            "mem_set_tuning": [P, I32, I32, I32], "mem_get_tuning": [P, P],
+            "mem_set_tuning": [P, I32, I32], "mem_get_tuning": [P, P],
             "mem_set_profiling": [P, I32], "mem_get_profile": [P, P, P], "mem_get_stats": [P, P, P],
             "mem_fuse_pointcloud_noalloc": [P, P, I64, P, P, P, P, P, P, P, P],
         }
@@ -275,14 +275,13 @@ class Map:
     def check(self, stream=None):
         _ck(lib().mem_check(self._h, _stream(stream)))
 
-    def set_tuning(self, radix_bits, small_max, blocks_per_sm):
-        _ck(lib().mem_set_tuning(self._h, radix_bits, small_max, blocks_per_sm))
+    def set_tuning(self, radix_bits, blocks_per_sm):
+        _ck(lib().mem_set_tuning(self._h, radix_bits, blocks_per_sm))
 
     def get_tuning(self):
         out = np.zeros(4, np.int32)
         _ck(lib().mem_get_tuning(self._h, out.ctypes.data))
-        return dict(radix_bits=int(out[0]), small_max=int(out[1]), blocks_per_sm=int(out[2]),
-                    passes=int(out[3]))
+        return dict(radix_bits=int(out[0]), blocks_per_sm=int(out[1]), passes=int(out[2]))
 
     def set_profiling(self, on: bool):
         _ck(lib().mem_set_profiling(self._h, int(on)))
@@ -297,5 +296,5 @@ class Map:
     def get_stats(self, stream=None):
         out = np.zeros(4, np.int64)
         _ck(lib().mem_get_stats(self._h, _stream(stream), out.ctypes.data))
-        return dict(short_cells=int(out[0]), long_cells=int(out[1]), kept=int(out[2]),
+        return dict(crossing_cells=int(out[0]), cells=int(out[1]), kept=int(out[2]),
                     passes=int(out[3]))

@@ -35,13 +35,13 @@ def test_config1_height_and_colour(torch):
     compare_states(gs, o, what="config 1")
 
 
-@pytest.mark.parametrize("radix_bits,small_max", [(8, 8), (9, 1), (10, 32), (9, 4)])
-def test_multimodal_scan_sequence(torch, radix_bits, small_max):
+@pytest.mark.parametrize("radix_bits,bps", [(8, 4), (9, 1), (10, 2), (9, 8)])
+def test_multimodal_scan_sequence(torch, radix_bits, bps):
     """Several poses of the multi-modal workload (reduced sensors), each step starting both
     sides from the same (oracle) state: move, then fuse, then compare."""
     c = synth.config2(n_poses=3, scale=0.25)
     g, o = make_pair(c["W"], c["res"], multimodal_layers(), max_points=1 << 16)
-    g.set_tuning(radix_bits, small_max, 4)
+    g.set_tuning(radix_bits, bps)
     for k, scan in enumerate(c["scans"]):
         upload_state(g, o)
         xy = c["poses"][k][:2]
