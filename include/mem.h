@@ -202,6 +202,17 @@ mem_status mem_set_tuning(mem_map *m, int32_t radix_bits, int32_t blocks_per_sm)
 /* out = {radix_bits, blocks_per_sm, radix passes, 0} (host). */
 mem_status mem_get_tuning(const mem_map *m, int32_t out[4]);
 
+/* Autotuner: times every schedule candidate (radix_bits in {8, 9, 10},
+ * blocks_per_sm in {2, 4, 8}) on this batched call (arguments as for
+ * mem_fuse_pointcloud_batch), `reps` timed runs each from the same saved map
+ * state, keeps the fastest and restores the state, so the map is unchanged.
+ * Allocates a temporary copy of the map state. ms_out (host, optional) gets
+ * the mean time of each candidate tried; *n_out (host, optional) its capacity
+ * on entry and the number of candidates tried on return. Synchronises. */
+mem_status mem_autotune_batch(mem_map *m, const int64_t *offsets, const float *xyz, int32_t n_sources,
+                              const mem_source *sources, const double *T_map_sensor, int32_t reps,
+                              void *stream, float *ms_out, int32_t *n_out);
+
 /* Per-kernel timing: with profiling on, every launch group of this map is
  * bracketed by CUDA events on its stream (graph replay is then disabled).
  * mem_get_profile waits for the recorded events and returns, per slot, the
@@ -215,6 +226,21 @@ mem_status mem_get_profile(mem_map *m, double ms[MEM_PROFILE_SLOTS], int64_t cal
  * the sorted order, touched cells, kept points, radix passes} of the last
  * point fuse (host output). */
 mem_status mem_get_stats(mem_map *m, void *stream, int64_t out[4]);
+
+/* Diffusion (harmonic) inpainting of a batch of map crops, the fallback of the
+ * learned inpainting and the reference it is judged against: each unknown
+ * cell (known == 0) becomes the mean of its in-crop 4-neighbours (zero-flux
+ * border) -- the discrete Laplace equation with the known cells as boundary
+ * values; known cells are copied. Solved in float32 by red-black successive
+ * over-relaxation from the mean of the crop's known cells, until the largest
+ * update of a sweep is below tol or after max_iters sweeps.
+ *   h_in, h_out  device float32 [n_crops][H][W] (may not alias)
+ *   known        device uint8 [n_crops][H][W]
+ *   iters_out    device int32 [n_crops] sweeps used (optional)
+ * A group of unknown cells with no known cell around it keeps the mean. */
+mem_status mem_inpaint_diffusion(int32_t n_crops, int32_t H, int32_t W, const float *h_in,
+                                 const uint8_t *known, float *h_out, float tol, int32_t max_iters,
+                                 int32_t *iters_out, void *stream);
 
 /* Allocation-free height fuse. The paper has no counterpart: this entry point
  * exists for callers that cannot call cudaMalloc -- code that runs inside

@@ -273,6 +273,54 @@ def bresenham(sx: int, sy: int, ex: int, ey: int) -> np.ndarray:
     return buf[:2 * n].reshape(n, 2)
 
 
+def harmonic_fill_exact(h: np.ndarray, known: np.ndarray) -> np.ndarray:
+    """The harmonic fill as its definition: for every unknown cell, (number of in-grid
+    4-neighbours) * x_j - sum of unknown neighbours = sum of known neighbours; solved directly
+    in float64 (sparse LU). Unknown cells with no known cell in their connected group keep the
+    mean of the known cells (the starting value of the iterative solvers)."""
+    import scipy.ndimage as ndi
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spl
+    h = np.asarray(h, dtype=np.float64)
+    kn = np.asarray(known).astype(bool)
+    H, W = h.shape
+    out = h.copy()
+    mean = h[kn].mean() if kn.any() else 0.0
+    unk = ~kn
+    if not unk.any():
+        return out
+    lab, nlab = ndi.label(unk)  # 4-connected groups of unknown cells
+    touch = np.zeros(nlab + 1, bool)
+    grow = ndi.binary_dilation(kn)  # unknown cells next to a known cell
+    touch[np.unique(lab[unk & grow])] = True
+    solve = unk & touch[lab]
+    out[unk & ~solve] = mean
+    n = int(solve.sum())
+    if n == 0:
+        return out
+    idx = -np.ones((H, W), np.int64)
+    idx[solve] = np.arange(n)
+    deg = np.zeros((H, W))
+    b = np.zeros((H, W))
+    rows, cols = [], []
+    for dy, dx in ((0, 1), (0, -1), (1, 0), (-1, 0)):
+        ys, xs = np.nonzero(solve)
+        ny, nx = ys + dy, xs + dx
+        ok = (ny >= 0) & (ny < H) & (nx >= 0) & (nx < W)
+        ys, xs, ny, nx = ys[ok], xs[ok], ny[ok], nx[ok]
+        np.add.at(deg, (ys, xs), 1.0)
+        nk = kn[ny, nx]
+        np.add.at(b, (ys[nk], xs[nk]), h[ny[nk], nx[nk]])
+        nu = ~nk
+        rows.append(idx[ys[nu], xs[nu]])
+        cols.append(idx[ny[nu], nx[nu]])
+    r = np.concatenate(rows)
+    c = np.concatenate(cols)
+    A = sp.csr_matrix((-np.ones(len(r)), (r, c)), shape=(n, n)) + sp.diags(deg[solve])
+    out[solve] = spl.spsolve(A.tocsc(), b[solve])
+    return out
+
+
 def harmonic_fill(h: np.ndarray, known: np.ndarray, tol: float = 1e-10, max_sweeps: int = 200000):
     h = np.ascontiguousarray(h, dtype=np.float64).copy()
     k = np.ascontiguousarray(known, dtype=np.uint8)

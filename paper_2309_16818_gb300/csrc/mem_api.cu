@@ -753,6 +753,107 @@ extern "C" mem_status mem_get_origin(const mem_map* mm, int32_t map_index, doubl
   return MEM_OK;
 }
 
+// Autotuner of the point path's schedule: every candidate (radix digit width x
+// persistent-grid size) runs the given batched call `reps` times from the same
+// saved map state; the fastest is kept and the state is restored.
+extern "C" mem_status mem_autotune_batch(mem_map* mm, const int64_t* offsets, const float* xyz,
+                                         int32_t n_sources, const mem_source* sources,
+                                         const double* T_map_sensor, int32_t reps, void* stream,
+                                         float* ms_out, int32_t* n_out) {
+  if (!mm || !offsets || !T_map_sensor) return fail(MEM_ERR_ARG, "NULL argument");
+  if (reps < 1 || reps > 1000) return fail(MEM_ERR_ARG, "reps in [1, 1000]");
+  Map* m = &mm->m;
+  cudaStream_t st = (cudaStream_t)stream;
+  // every state array of the map, saved once
+  std::vector<std::pair<void*, size_t>> arrays;
+  const size_t cells = (size_t)m->cfg.n_maps * m->md.W2;
+  arrays.push_back({m->md.h, cells * 4});
+  arrays.push_back({m->md.var, cells * 4});
+  arrays.push_back({m->md.flags, cells * 4});
+  arrays.push_back({m->md.n_acc, cells * 4});
+  arrays.push_back({m->md.n_rej, cells * 4});
+  for (int l = 0; l < m->cfg.n_layers; ++l) {
+    arrays.push_back({m->Lh[l].data, cells * m->Lh[l].S * dtype_size(m->Lh[l].dtype)});
+    if (m->Lh[l].gvar) arrays.push_back({m->Lh[l].gvar, cells * 4});
+  }
+  size_t total = 0;
+  for (auto& a : arrays) total += (a.second + 255) & ~(size_t)255;
+  char* backup = nullptr;
+  CK(cudaMalloc(&backup, total), "autotune backup");
+  auto copy_all = [&](bool save) -> cudaError_t {
+    size_t o = 0;
+    for (auto& a : arrays) {
+      cudaError_t e = save ? cudaMemcpyAsync(backup + o, a.first, a.second, cudaMemcpyDeviceToDevice, st)
+                           : cudaMemcpyAsync(a.first, backup + o, a.second, cudaMemcpyDeviceToDevice, st);
+      if (e != cudaSuccess) return e;
+      o += (a.second + 255) & ~(size_t)255;
+    }
+    return cudaSuccess;
+  };
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const Tuning saved = m->tune;
+  const int saved_passes = m->passes;
+  float best = 1e30f;
+  Tuning best_t = saved;
+  int count = 0;
+  mem_status s = MEM_OK;
+  cudaError_t ce = copy_all(true);
+  const int bits_opts[3] = {8, 9, 10}, bps_opts[3] = {2, 4, 8};
+  for (int bi = 0; bi < 3 && ce == cudaSuccess && s == MEM_OK; ++bi) {
+    const int passes = (m->key_bits + bits_opts[bi] - 1) / bits_opts[bi];
+    if (passes > 4) continue;
+    for (int pi = 0; pi < 3 && ce == cudaSuccess && s == MEM_OK; ++pi) {
+      cudaStreamSynchronize(st);
+      m->tune.radix_bits = bits_opts[bi];
+      m->tune.blocks_per_sm = bps_opts[pi];
+      m->passes = passes;
+      if (m->graph) {
+        cudaGraphExecDestroy(m->graph);
+        m->graph = nullptr;
+      }
+      float acc_ms = 0.f;
+      for (int r = 0; r <= reps && s == MEM_OK; ++r) {  // r = 0 warms up (and captures the graph)
+        if ((ce = copy_all(false)) != cudaSuccess) break;
+        cudaEventRecord(e0, st);
+        s = mem_fuse_pointcloud_batch(mm, offsets, xyz, n_sources, sources, T_map_sensor, stream);
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        if (r > 0) acc_ms += t;
+      }
+      if (s != MEM_OK || ce != cudaSuccess) break;
+      const float ms = acc_ms / reps;
+      if (ms_out && n_out && count < *n_out) ms_out[count] = ms;
+      ++count;
+      if (ms < best) {
+        best = ms;
+        best_t = m->tune;
+      }
+    }
+  }
+  cudaStreamSynchronize(st);
+  m->tune = (s == MEM_OK && ce == cudaSuccess) ? best_t : saved;
+  m->passes = (s == MEM_OK && ce == cudaSuccess) ? (m->key_bits + m->tune.radix_bits - 1) / m->tune.radix_bits
+                                                 : saved_passes;
+  if (m->graph) {
+    cudaGraphExecDestroy(m->graph);
+    m->graph = nullptr;
+  }
+  cudaError_t ce2 = copy_all(false);
+  cudaStreamSynchronize(st);
+  cudaFree(backup);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (n_out) *n_out = count;
+  if (s != MEM_OK) return s;
+  if (ce != cudaSuccess) return cuda_fail(ce, "autotune state copy");
+  if (ce2 != cudaSuccess) return cuda_fail(ce2, "autotune state restore");
+  return MEM_OK;
+}
+
 extern "C" mem_status mem_set_profiling(mem_map* mm, int32_t on) {
   if (!mm) return fail(MEM_ERR_ARG, "NULL argument");
   mm->m.prof_on = on != 0;

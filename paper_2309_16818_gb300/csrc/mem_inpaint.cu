@@ -1,0 +1,125 @@
+// Diffusion (harmonic) inpainting of map crops: every unknown cell takes the
+// mean of its in-crop 4-neighbours (zero-flux border), known cells stay fixed,
+// i.e. the discrete Laplace equation with the known cells as boundary values.
+//
+// One thread block owns one crop, so the red-black successive
+// over-relaxation sweeps only need block barriers; a crop of 256 x 256 float32
+// values is 256 KB, and a batch of them stays resident in the 129 MB L2.
+// Unknown cells start from the mean of the crop's known cells; the sweeps stop
+// when the largest update of a full sweep falls below `tol` or after
+// `max_iters` sweeps.
+#include <math.h>
+
+#include "mem_host.h"
+
+namespace memk {
+
+constexpr int kInpThreads = 1024;
+
+__device__ __forceinline__ float block_max(float v, float* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    v = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0) red[32] = v;
+  }
+  __syncthreads();
+  const float r = red[32];
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ float block_sum(float v, float* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    v = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[32] = v;
+  }
+  __syncthreads();
+  const float r = red[32];
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(kInpThreads) k_inpaint_sor(int H, int W, const float* __restrict__ hin,
+                                                             const uint8_t* __restrict__ known,
+                                                             float* __restrict__ hout, float omega, float tol,
+                                                             int max_iters, int* iters_out) {
+  __shared__ float red[33];
+  const int64_t base = (int64_t)blockIdx.x * H * W;
+  const float* in = hin + base;
+  const uint8_t* kn = known + base;
+  float* h = hout + base;
+  const int n = H * W;
+  // initial guess: known values, unknown cells at the mean of the known ones
+  float s = 0.f, c = 0.f;
+  for (int j = threadIdx.x; j < n; j += blockDim.x)
+    if (kn[j]) {
+      s += in[j];
+      c += 1.f;
+    }
+  s = block_sum(s, red);
+  c = block_sum(c, red);
+  const float mean = c > 0.f ? s / c : 0.f;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) h[j] = kn[j] ? in[j] : mean;
+  __syncthreads();
+  int it = 0;
+  for (; it < max_iters; ++it) {
+    float dmax = 0.f;
+    for (int color = 0; color < 2; ++color) {
+      for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const int y = j / W, x = j - y * W;
+        if (((x + y) & 1) != color || kn[j]) continue;
+        float sum = 0.f;
+        int m = 0;
+        if (x > 0) sum += h[j - 1], ++m;
+        if (x + 1 < W) sum += h[j + 1], ++m;
+        if (y > 0) sum += h[j - W], ++m;
+        if (y + 1 < H) sum += h[j + W], ++m;
+        if (m == 0) continue;  // a 1 x 1 crop keeps its starting value
+        const float old = h[j];
+        const float d = sum / (float)m - old;
+        h[j] = fmaf(omega, d, old);
+        dmax = fmaxf(dmax, fabsf(d));
+      }
+      __syncthreads();
+    }
+    dmax = block_max(dmax, red);
+    if (dmax < tol) {
+      ++it;
+      break;
+    }
+  }
+  if (threadIdx.x == 0 && iters_out) iters_out[blockIdx.x] = it;
+}
+
+}  // namespace memk
+
+extern "C" mem_status mem_inpaint_diffusion(int32_t n_crops, int32_t H, int32_t W, const float* h_in,
+                                            const uint8_t* known, float* h_out, float tol,
+                                            int32_t max_iters, int32_t* iters_out, void* stream) {
+  if (n_crops < 0 || H < 1 || W < 1 || (int64_t)H * W > (1 << 24))
+    return memh::api_fail(MEM_ERR_ARG, "bad crop shape");
+  if (n_crops > 0 && (!h_in || !known || !h_out)) return memh::api_fail(MEM_ERR_ARG, "NULL argument");
+  if (!(tol > 0.f) || max_iters < 1) return memh::api_fail(MEM_ERR_ARG, "tol > 0 and max_iters >= 1");
+  if (n_crops == 0) return MEM_OK;
+  // optimal over-relaxation of the model problem on the longer side
+  const int L = H > W ? H : W;
+  const float omega = (float)(2.0 / (1.0 + sin(M_PI / (double)(L + 1))));
+  memk::k_inpaint_sor<<<n_crops, memk::kInpThreads, 0, (cudaStream_t)stream>>>(
+      H, W, h_in, known, h_out, omega, tol, max_iters, iters_out);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return memh::api_cuda_fail(e, "inpaint launch");
+  return MEM_OK;
+}

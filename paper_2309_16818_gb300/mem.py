@@ -26,7 +26,8 @@ PART_VALUE, PART_THETA, PART_VAR, PART_OBSERVED = range(4)
 EXPORTS = ["mem_create_map", "mem_destroy_map", "mem_move_map", "mem_fuse_pointcloud",
            "mem_fuse_pointcloud_batch", "mem_fuse_image", "mem_get_layer", "mem_set_layer",
            "mem_get_origin", "mem_check", "mem_last_error", "mem_set_tuning", "mem_get_tuning",
-           "mem_set_profiling", "mem_get_profile", "mem_get_stats", "mem_fuse_pointcloud_noalloc"]
+           "mem_set_profiling", "mem_get_profile", "mem_get_stats", "mem_fuse_pointcloud_noalloc",
+           "mem_autotune_batch", "mem_inpaint_diffusion"]
 NOALLOC_MAX_POINTS = 1 << 18
 PROFILE_SLOTS = ["key", "digit_scan", "radix_sort", "segments", "fuse_window", "fuse_span",
                  "time_var", "image", "move"]
@@ -79,6 +80,8 @@ def lib():
             "mem_set_tuning": [P, I32, I32], "mem_get_tuning": [P, P],
             "mem_set_profiling": [P, I32], "mem_get_profile": [P, P, P], "mem_get_stats": [P, P, P],
             "mem_fuse_pointcloud_noalloc": [P, P, I64, P, P, P, P, P, P, P, P],
+            "mem_autotune_batch": [P, P, P, I32, P, P, I32, P, P, P],
+            "mem_inpaint_diffusion": [I32, I32, I32, P, P, P, C.c_float, I32, P, P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -137,6 +140,22 @@ def fuse_pointcloud_noalloc(W, res, xyz, T, h, var, valid, n_acc, n_rej, origin=
                                           C.c_void_p(h.data_ptr()), C.c_void_p(var.data_ptr()),
                                           C.c_void_p(valid.data_ptr()), C.c_void_p(n_acc.data_ptr()),
                                           C.c_void_p(n_rej.data_ptr()), _stream(stream)))
+
+
+def inpaint_diffusion(h, known, tol=1e-6, max_iters=20000, out=None, stream=None):
+    """Harmonic fill of unknown cells: h float32 [B,H,W] cuda, known uint8 [B,H,W] cuda.
+    Returns (filled float32 [B,H,W], sweeps used int32 [B])."""
+    torch = _torch()
+    assert h.is_cuda and h.dtype == torch.float32 and h.is_contiguous() and h.dim() == 3
+    assert known.is_cuda and known.dtype == torch.uint8 and known.shape == h.shape and known.is_contiguous()
+    B, H, W = h.shape
+    if out is None:
+        out = torch.empty_like(h)
+    its = torch.zeros(B, dtype=torch.int32, device=h.device)
+    _ck(lib().mem_inpaint_diffusion(B, H, W, C.c_void_p(h.data_ptr()), C.c_void_p(known.data_ptr()),
+                                    C.c_void_p(out.data_ptr()), tol, max_iters,
+                                    C.c_void_p(its.data_ptr()), _stream(stream)))
+    return out, its
 
 
 @dataclass
@@ -282,6 +301,21 @@ class Map:
         out = np.zeros(4, np.int32)
         _ck(lib().mem_get_tuning(self._h, out.ctypes.data))
         return dict(radix_bits=int(out[0]), blocks_per_sm=int(out[1]), passes=int(out[2]))
+
+    def autotune_batch(self, offsets, xyz, T, sources=(), reps=3, stream=None):
+        """Pick the fastest schedule for this batched call; the map state is left unchanged.
+        Returns (chosen tuning, list of candidate times in ms)."""
+        keep = []
+        src = self._sources(list(sources), keep)
+        off = np.ascontiguousarray(offsets, dtype=np.int64)
+        Tb = _pose(T, self.n_maps)
+        ms = np.zeros(16, np.float32)
+        n = C.c_int32(16)
+        _ck(lib().mem_autotune_batch(self._h, off.ctypes.data,
+                                     C.c_void_p(xyz.data_ptr() if xyz.numel() else 0), len(sources),
+                                     src, Tb.ctypes.data, reps, _stream(stream), ms.ctypes.data,
+                                     C.byref(n)))
+        return self.get_tuning(), [float(x) for x in ms[:n.value]]
 
     def set_profiling(self, on: bool):
         _ck(lib().mem_set_profiling(self._h, int(on)))

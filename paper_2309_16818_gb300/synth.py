@@ -357,6 +357,45 @@ def config4(n_maps: int = 512, seed_base: int = 10_000, n_lo: int = 5_000, n_hi:
     return dict(W=W, res=res, clouds=clouds, offsets=offsets)
 
 
+# ----------------------------------------------------------------------------
+# configuration 5: crops of height maps with occlusion holes
+
+
+def line_of_sight(terrain: Terrain, sensor, X, Y, Z, n_steps: int = 96) -> np.ndarray:
+    """True where the straight segment from the sensor to (X, Y, Z) stays above the continuous
+    terrain (dense float64 march; a sensor simulation, not a map computation)."""
+    s = np.asarray(sensor, dtype=np.float64)
+    t = (np.arange(1, n_steps) / n_steps)[:, None, None]
+    px = s[0] + t * (X[None] - s[0])
+    py = s[1] + t * (Y[None] - s[1])
+    pz = s[2] + t * (Z[None] - s[2])
+    return np.all(pz > terrain.height(px, py) + 1e-9, axis=0)
+
+
+def inpaint_crops(n: int, size: int = 256, res: float = 0.05, seed: int = 0, lo: float = 0.10,
+                  hi: float = 0.60, sensor_height=(0.3, 1.2)):
+    """n crops (size x size cells) of terrain heights with the cells hidden from a random sensor
+    pose removed (occlusion holes); the hidden fraction is rejection-sampled into [lo, hi].
+    Returns heights float32 [n,S,S] (the full, ground-truth field) and known uint8 [n,S,S]."""
+    rng = np.random.default_rng(seed)
+    hs, ks = [], []
+    ext = size * res
+    xs = (np.arange(size) - size / 2 + 0.5) * res
+    X, Y = np.meshgrid(xs, xs)
+    while len(hs) < n:
+        ter = Terrain.from_seed(int(rng.integers(0, 2**31)))
+        Z = ter.height(X, Y)
+        sx, sy = rng.uniform(-ext / 2, ext / 2, size=2)
+        sz = float(ter.height(sx, sy)) + float(rng.uniform(*sensor_height))
+        vis = line_of_sight(ter, (sx, sy, sz), X, Y, Z)
+        frac = 1.0 - vis.mean()
+        if not (lo <= frac <= hi):
+            continue
+        hs.append(Z.astype(np.float32))
+        ks.append(vis.astype(np.uint8))
+    return np.stack(hs), np.stack(ks)
+
+
 def concat_clouds(clouds):
     xyz = np.concatenate([c.xyz for c in clouds], axis=0)
     rgb = np.concatenate([c.rgb for c in clouds], axis=0) if clouds[0].rgb is not None else None

@@ -233,3 +233,30 @@ def test_harmonic_fill_constant_and_maximum_principle():
     g = rng.normal(size=(H, W))
     out, _, _ = O.harmonic_fill(np.where(known, g, 0.0), known, tol=1e-12)
     assert out.min() >= g[known].min() - 1e-9 and out.max() <= g[known].max() + 1e-9
+
+
+def test_exact_harmonic_fill_pins():
+    """The direct solve reproduces linear fields and constants, obeys the maximum principle and
+    agrees with the Gauss-Seidel sweeps of the C oracle."""
+    rng = np.random.default_rng(5)
+    H, W = 40, 36
+    y, x = np.mgrid[0:H, 0:W]
+    f = -0.2 * x + 0.45 * y + 1.0
+    known = _hole(H, W, rng, frac=0.5)
+    out = O.harmonic_fill_exact(np.where(known, f, 7.0), known)
+    np.testing.assert_allclose(out, f, atol=1e-10)
+    g = rng.normal(size=(H, W))
+    known = _hole(H, W, rng, frac=0.6, border=0)
+    known[5, 5] = True
+    ex = O.harmonic_fill_exact(np.where(known, g, 0.0), known)
+    gs, _, r = O.harmonic_fill(np.where(known, g, 0.0), known, tol=1e-13)
+    np.testing.assert_allclose(ex, gs, atol=1e-9)
+    assert ex.min() >= g[known].min() - 1e-12 and ex.max() <= g[known].max() + 1e-12
+    # a group of unknown cells with no known neighbour keeps the mean of the known cells
+    kn = np.zeros((8, 8), bool)
+    kn[:, :2] = True
+    kn[:, 2] = False
+    kn[4, 2] = False
+    h0 = np.arange(64, dtype=float).reshape(8, 8)
+    out = O.harmonic_fill_exact(h0, kn)
+    np.testing.assert_allclose(out[kn], h0[kn])
