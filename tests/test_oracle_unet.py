@@ -1,0 +1,92 @@
+"""Pins of the float64 U-Net oracle: central finite differences of the loss against the
+backward pass, the adjoint identities of its building blocks, and the residual design (a zero
+output layer returns the diffusion fill exactly). CPU only."""
+import numpy as np
+import pytest
+
+from oracle import unet as U
+
+WIDTHS = (4, 6, 6, 8)
+
+
+def _setup(seed=0, N=2, H=16, W=16, cin=3):
+    rng = np.random.default_rng(seed)
+    p = U.init_params(rng, cin, WIDTHS)
+    x = rng.normal(size=(N, H, W, cin))
+    fill = rng.normal(size=(N, H, W))
+    target = rng.normal(size=(N, H, W))
+    hidden = (rng.random((N, H, W)) < 0.4).astype(float)
+    return p, x, fill, target, hidden
+
+
+def _loss(p, x, fill, target, hidden):
+    res, _ = U.forward(p, x, WIDTHS)
+    return U.loss_and_grad_out(res, fill, target, hidden)[0]
+
+
+def test_im2col_col2im_adjoint():
+    rng = np.random.default_rng(1)
+    x = rng.normal(size=(2, 5, 7, 3))
+    c = rng.normal(size=(2 * 5 * 7, 27))
+    assert np.isclose((U.im2col(x) * c).sum(), (x * U.col2im(c, x.shape)).sum(), rtol=1e-12)
+
+
+def test_pool_and_upsample_adjoints():
+    rng = np.random.default_rng(2)
+    x = rng.normal(size=(2, 6, 8, 3))
+    dy = rng.normal(size=(2, 3, 4, 3))
+    u = rng.normal(size=(2, 6, 8, 3))
+    assert np.isclose((U.upsample(dy) * u).sum(), (dy * U.upsample_backward(u)).sum(), rtol=1e-12)
+    g = U.maxpool_backward(x, dy)
+    # the gradient lands on the window maxima only and sums to dy per window
+    assert np.allclose(U.upsample_backward(g), dy)
+    assert np.all((g != 0) <= (x == U.upsample(U.maxpool(x))))
+
+
+def test_conv_matches_direct_loops():
+    rng = np.random.default_rng(3)
+    x = rng.normal(size=(1, 4, 5, 2))
+    w = rng.normal(size=(3, 3, 2, 3))
+    b = rng.normal(size=3)
+    y = U.conv3x3(x, w, b)
+    for yy in range(4):
+        for xx in range(5):
+            for co in range(3):
+                s = b[co]
+                for ky in range(3):
+                    for kx in range(3):
+                        sy, sx = yy + ky - 1, xx + kx - 1
+                        if 0 <= sy < 4 and 0 <= sx < 5:
+                            s += x[0, sy, sx] @ w[ky, kx, :, co]
+                assert np.isclose(y[0, yy, xx, co], s, rtol=1e-12)
+
+
+@pytest.mark.parametrize("name", ["e1a.w", "e2b.w", "e4a.b", "d3a.w", "d1b.w", "out.w", "out.b"])
+def test_gradients_central_differences(name):
+    p, x, fill, target, hidden = _setup()
+    res, a = U.forward(p, x, WIDTHS)
+    _, dres = U.loss_and_grad_out(res, fill, target, hidden)
+    g = U.backward(p, a, dres, WIDTHS)
+    rng = np.random.default_rng(4)
+    flat = p[name].reshape(-1)
+    for k in rng.choice(flat.size, size=min(6, flat.size), replace=False):
+        eps = 1e-6
+        old = flat[k]
+        flat[k] = old + eps
+        lp = _loss(p, x, fill, target, hidden)
+        flat[k] = old - eps
+        lm = _loss(p, x, fill, target, hidden)
+        flat[k] = old
+        fd = (lp - lm) / (2 * eps)
+        an = g[name].reshape(-1)[k]
+        assert abs(fd - an) <= 1e-6 * max(1.0, abs(fd)) + 1e-9, (name, k, fd, an)
+
+
+def test_zero_output_layer_returns_fill():
+    p, x, fill, target, hidden = _setup(5)
+    p["out.w"][:] = 0
+    p["out.b"][:] = 0
+    res, _ = U.forward(p, x, WIDTHS)
+    assert np.all(res == 0)
+    pred = fill + res
+    assert np.array_equal(pred, fill)
