@@ -242,6 +242,39 @@ mem_status mem_inpaint_diffusion(int32_t n_crops, int32_t H, int32_t W, const fl
                                  const uint8_t *known, float *h_out, float tol, int32_t max_iters,
                                  int32_t *iters_out, void *stream);
 
+/* Learned inpainting (the paper's post-processing plugins "take map layers as
+ * input and generate a new layer", Sec. III-D; the network layout is this
+ * library's): a U-Net over crops of map layers predicting a residual that is
+ * added to the diffusion fill. Four levels of widths[0..3] channels, two 3x3
+ * convolutions + ReLU per level, 2x2 max-pooling, nearest upsampling with
+ * skip concatenation [upsampled, skip], a final 1x1 convolution. BF16
+ * tensor-core kernels with float32 accumulation; float32 master weights.
+ * Parameters (flat float32, in this order): for each 3x3 convolution
+ * e1a e1b e2a e2b e3a e3b e4a e4b d3a d3b d2a d2b d1a d1b its weights
+ * [3][3][C_in][C_out] then bias [C_out]; then the 1x1 weights [widths[0]] and
+ * bias [1]. Crops are NHWC: x3 = float32 [n][H][W][cin] inputs, fill /
+ * target / pred = float32 [n][H][W], hidden = uint8 [n][H][W] (1 = cell whose
+ * value the loss scores); H and W multiples of 8. All pointers device. */
+typedef struct mem_unet mem_unet;
+mem_status mem_unet_create(int32_t cin, const int32_t widths[4], mem_unet **out);
+mem_status mem_unet_destroy(mem_unet *u);
+mem_status mem_unet_param_count(const mem_unet *u, int64_t *n);
+mem_status mem_unet_set_params(mem_unet *u, const float *src, void *stream);
+mem_status mem_unet_get_params(const mem_unet *u, float *dst, void *stream);
+/* pred = fill + residual(x3) */
+mem_status mem_unet_forward(mem_unet *u, int32_t n, int32_t H, int32_t W, const float *x3,
+                            const float *fill, float *pred, void *stream);
+/* loss = sum over hidden cells of (pred - target)^2 / n_hidden (device
+ * float32, optional) and its gradient for every parameter into grads (flat,
+ * optional) */
+mem_status mem_unet_gradients(mem_unet *u, int32_t n, int32_t H, int32_t W, const float *x3,
+                              const float *fill, const float *target, const uint8_t *hidden,
+                              int64_t n_hidden, float *grads, float *loss, void *stream);
+/* one Adam step (beta 0.9, 0.999) with learning rate lr on that loss */
+mem_status mem_unet_train_step(mem_unet *u, int32_t n, int32_t H, int32_t W, const float *x3,
+                               const float *fill, const float *target, const uint8_t *hidden,
+                               int64_t n_hidden, float lr, float *loss, void *stream);
+
 /* Allocation-free height fuse. The paper has no counterpart: this entry point
  * exists for callers that cannot call cudaMalloc -- code that runs inside
  * another framework's memory pool, real-time loops that forbid allocation

@@ -27,7 +27,9 @@ EXPORTS = ["mem_create_map", "mem_destroy_map", "mem_move_map", "mem_fuse_pointc
            "mem_fuse_pointcloud_batch", "mem_fuse_image", "mem_get_layer", "mem_set_layer",
            "mem_get_origin", "mem_check", "mem_last_error", "mem_set_tuning", "mem_get_tuning",
            "mem_set_profiling", "mem_get_profile", "mem_get_stats", "mem_fuse_pointcloud_noalloc",
-           "mem_autotune_batch", "mem_inpaint_diffusion"]
+           "mem_autotune_batch", "mem_inpaint_diffusion", "mem_unet_create", "mem_unet_destroy",
+           "mem_unet_param_count", "mem_unet_set_params", "mem_unet_get_params", "mem_unet_forward",
+           "mem_unet_gradients", "mem_unet_train_step"]
 NOALLOC_MAX_POINTS = 1 << 18
 PROFILE_SLOTS = ["key", "digit_scan", "radix_sort", "segments", "fuse_window", "fuse_span",
                  "time_var", "image", "move"]
@@ -82,6 +84,11 @@ def lib():
             "mem_fuse_pointcloud_noalloc": [P, P, I64, P, P, P, P, P, P, P, P],
             "mem_autotune_batch": [P, P, P, I32, P, P, I32, P, P, P],
             "mem_inpaint_diffusion": [I32, I32, I32, P, P, P, C.c_float, I32, P, P],
+            "mem_unet_create": [I32, P, P], "mem_unet_destroy": [P], "mem_unet_param_count": [P, P],
+            "mem_unet_set_params": [P, P, P], "mem_unet_get_params": [P, P, P],
+            "mem_unet_forward": [P, I32, I32, I32, P, P, P, P],
+            "mem_unet_gradients": [P, I32, I32, I32, P, P, P, P, I64, P, P, P],
+            "mem_unet_train_step": [P, I32, I32, I32, P, P, P, P, I64, C.c_float, P, P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -332,3 +339,70 @@ class Map:
         _ck(lib().mem_get_stats(self._h, _stream(stream), out.ctypes.data))
         return dict(crossing_cells=int(out[0]), cells=int(out[1]), kept=int(out[2]),
                     passes=int(out[3]))
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
+
+
+class UNet:
+    """Inpainting U-Net on the library's BF16 tensor-core kernels (mem_unet_*)."""
+
+    def __init__(self, cin=3, widths=(32, 64, 128, 128)):
+        self.cin, self.widths = cin, tuple(widths)
+        w = (C.c_int32 * 4)(*widths)
+        self._h = C.c_void_p()
+        _ck(lib().mem_unet_create(cin, w, C.byref(self._h)))
+        n = C.c_int64()
+        _ck(lib().mem_unet_param_count(self._h, C.byref(n)))
+        self.n_params = n.value
+
+    def close(self):
+        if self._h:
+            lib().mem_unet_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, flat, stream=None):
+        torch = _torch()
+        assert flat.is_cuda and flat.dtype == torch.float32 and flat.numel() == self.n_params
+        _ck(lib().mem_unet_set_params(self._h, _ptr(flat.contiguous()), _stream(stream)))
+
+    def get_params(self, stream=None):
+        torch = _torch()
+        out = torch.empty(self.n_params, dtype=torch.float32, device="cuda")
+        _ck(lib().mem_unet_get_params(self._h, _ptr(out), _stream(stream)))
+        return out
+
+    def forward(self, x3, fill, out=None, stream=None):
+        torch = _torch()
+        n, H, W, _ = x3.shape
+        if out is None:
+            out = torch.empty((n, H, W), dtype=torch.float32, device="cuda")
+        _ck(lib().mem_unet_forward(self._h, n, H, W, _ptr(x3), _ptr(fill), _ptr(out), _stream(stream)))
+        return out
+
+    def gradients(self, x3, fill, target, hidden, stream=None):
+        torch = _torch()
+        n, H, W, _ = x3.shape
+        g = torch.empty(self.n_params, dtype=torch.float32, device="cuda")
+        loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+        nh = int(hidden.sum().item())
+        _ck(lib().mem_unet_gradients(self._h, n, H, W, _ptr(x3), _ptr(fill), _ptr(target), _ptr(hidden), nh,
+                                     _ptr(g), _ptr(loss), _stream(stream)))
+        return g, loss
+
+    def train_step(self, x3, fill, target, hidden, lr, n_hidden=None, loss=None, stream=None):
+        torch = _torch()
+        n, H, W, _ = x3.shape
+        if loss is None:
+            loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+        nh = int(hidden.sum().item()) if n_hidden is None else int(n_hidden)
+        _ck(lib().mem_unet_train_step(self._h, n, H, W, _ptr(x3), _ptr(fill), _ptr(target), _ptr(hidden), nh,
+                                      lr, _ptr(loss), _stream(stream)))
+        return loss
