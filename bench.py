@@ -337,6 +337,8 @@ def run_ours(args):
         extra["batched"] = bench_batched(args, dev, flush, ws)
     if not args.no_image:
         extra["image"] = bench_image(args, dev, flush, ws, c)
+    if not args.no_inpaint:
+        extra["inpainting"] = bench_inpaint(args, dev, flush, ws)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -397,6 +399,7 @@ def bench_batched(args, dev, flush, ws):
         torch.cuda.synchronize()
         return sum(a.elapsed_time(b) for a, b in evs) / 1e3 / reps
 
+    tuning, cand_ms = mb.autotune_batch(c["offsets"], dx, T, srcs, reps=2)
     t_batch = timed(lambda: mb.fuse_pointcloud_batch(c["offsets"], dx, T, srcs))
     mb.check()
     prof_b = None
@@ -429,7 +432,71 @@ def bench_batched(args, dev, flush, ws):
             "batched_points_per_s": round(ws * n / t_batch, 1),
             "speedup": round(t_plain / t_batch, 3), "ms_batched": round(1e3 * t_batch, 4),
             "ms_plain_512_calls": round(1e3 * t_plain, 4), "hbm_frac": round(algo / t_batch / 1e9 / peak, 4),
-            "kernels_ms": prof_b}
+            "kernels_ms": prof_b, "autotuned": tuning,
+            "autotune_candidates_ms": [round(x, 4) for x in cand_ms]}
+
+
+def bench_inpaint(args, dev, flush, ws):
+    """Diffusion fill and U-Net inference of 256 crops of 256 x 256 cells (the inference batch),
+    plus one training step on 16 crops; FLOPs of the 3x3 convolutions (2 per multiply-add)."""
+    import torch
+    from paper_2309_16818_gb300 import inpaint as I
+    from paper_2309_16818_gb300 import mem as M
+    from paper_2309_16818_gb300 import synth
+    S, B = 256, args.inpaint_crops
+    gt, kn = synth.inpaint_crops(8, size=S, seed=21)
+    rep = (B + 7) // 8
+    gt = np.concatenate([gt] * rep)[:B]
+    kn = np.concatenate([kn] * rep)[:B]
+    h = torch.from_numpy(np.where(kn == 1, gt, 0.0).astype(np.float32)).to(dev)
+    k = torch.from_numpy(kn).to(dev)
+    t = torch.from_numpy(gt).to(dev)
+    stream = torch.cuda.current_stream()
+    widths = (32, 64, 128, 128)
+    net = M.UNet(3, widths)
+    net.set_params(torch.from_numpy(I.init_params(0, 3, widths)).to(dev))
+
+    def ev(fn):
+        flush(0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        out = fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / 1e3, out
+
+    t_fill, (fill, its) = ev(lambda: M.inpaint_diffusion(h, k, tol=1e-6))
+    x3, fill, hidden, _ = I.prepare(h, k, tol=1e-6)
+    pred = torch.empty_like(fill)
+    net.forward(x3, fill, out=pred)  # warm-up (allocates activations)
+    t_inf, _ = ev(lambda: net.forward(x3, fill, out=pred))
+    c1, c2, c3, c4 = widths
+    macs = 0
+    for lvl, convs in enumerate([[(3, c1), (c1, c1), (c2 + c1, c1), (c1, c1)],
+                                 [(c1, c2), (c2, c2), (c3 + c2, c2), (c2, c2)],
+                                 [(c2, c3), (c3, c3), (c4 + c3, c3), (c3, c3)],
+                                 [(c3, c4), (c4, c4)]]):
+        px = (S >> lvl) ** 2
+        macs += sum(px * 9 * ci * co for ci, co in convs)
+    flops = 2.0 * macs * B
+    nb = 16
+    xs, fs, ts, hs = x3[:nb].contiguous(), fill[:nb].contiguous(), t[:nb].contiguous(), hidden[:nb].contiguous()
+    nh = int(hs.sum().item())
+    loss = torch.zeros(1, dtype=torch.float32, device=dev)
+    net.train_step(xs, fs, ts, hs, lr=1e-4, n_hidden=nh, loss=loss)
+    t_train, _ = ev(lambda: net.train_step(xs, fs, ts, hs, lr=1e-4, n_hidden=nh, loss=loss))
+    peaks_bf16 = 1956.5
+    try:
+        peaks_bf16 = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])
+    except Exception:
+        pass
+    tf = flops / t_inf / 1e12
+    return {"workload": f"{B} crops of {S}x{S} cells (height fill, hidden mask, log variance), U-Net widths {widths}",
+            "diffusion_ms": round(1e3 * t_fill, 3), "diffusion_max_sweeps": int(its.max().item()),
+            "unet_inference_ms": round(1e3 * t_inf, 3), "unet_inference_crops_per_s": round(ws * B / t_inf, 1),
+            "unet_conv_tflops": round(tf, 1), "unet_conv_frac_of_bf16_peak": round(tf / peaks_bf16, 4),
+            "unet_train_step_ms_16_crops": round(1e3 * t_train, 3),
+            "note": "3x3 convolutions run on mma.sync m16n8k16 BF16 tensor-core instructions"}
 
 
 def bench_image(args, dev, flush, ws, c2):
@@ -539,6 +606,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-image", action="store_true")
+    ap.add_argument("--no-inpaint", action="store_true")
+    ap.add_argument("--inpaint-crops", type=int, default=256)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--batch-maps", type=int, default=512)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
