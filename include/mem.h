@@ -155,6 +155,7 @@ mem_status mem_move_map(mem_map *m, int32_t map_index, const double robot_xy[2],
  *   sources  host array of n_sources (<= MEM_MAX_SOURCES) descriptors whose
  *            `data` are device [n][channels] rows
  *   T_map_sensor host float64 4x4 sensor -> world
+ * A layer may be listed by at most one source of a call (else MEM_ERR_ARG).
  * Steps: transform + range filter + cell key; stable radix sort of the keys;
  * per-cell height update with outlier gate; per-layer fusion rules. */
 mem_status mem_fuse_pointcloud(mem_map *m, int64_t n, const float *xyz, int32_t n_sources,
@@ -283,7 +284,7 @@ mem_status mem_unet_train_step(mem_unet *u, int32_t n, int32_t H, int32_t W, con
  * with outlier gate of mem_fuse_pointcloud, no multi-modal layers) and
  * allocates nothing: no cudaMalloc, cudaFree, pinned memory or allocating
  * library routine. Its sort and segment scratch is one file-scope device
- * array sized for MEM_NOALLOC_MAX_POINTS points (about 9.5 MB, held by every
+ * array sized for MEM_NOALLOC_MAX_POINTS points (about 22 MB, held by every
  * GPU that loads the library until the process exits).
  *   cfg       host; n_maps must be 1 and n_layers 0; max_points is ignored
  *   origin_xy host; world xy of the map centre (cell W/2 lower corner)

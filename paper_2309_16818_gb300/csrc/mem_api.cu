@@ -251,10 +251,10 @@ cudaError_t alloc_scratch(Map* m, int64_t cap) {
   return cudaSuccess;
 }
 
-// partial records of window-crossing runs: 2 per 32-point window, acc floats each
+// fuse scratch: tile tables and one slot of acc words per run piece
 static cudaError_t ensure_partial(Map* m, int acc) {
   MapDev& md = m->md;
-  const int64_t need = 2 * (md.cap / 32 + 2) * (int64_t)acc;
+  const int64_t need = fuse_scratch_words(md.cap, acc);
   if (need <= md.partial_cap) return cudaSuccess;
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return e;
@@ -557,6 +557,10 @@ static mem_status check_sources(const Map* m, int32_t n_sources, const mem_sourc
                     m->cfg.layers[l].channels);
       for (int b2 = 0; b2 < b; ++b2)
         if (s.layers[b2] == l) return fail(MEM_ERR_ARG, "source %d: layer %d listed twice", q, l);
+      for (int q2 = 0; q2 < q && !image; ++q2)
+        for (int b2 = 0; b2 < sources[q2].n_layers; ++b2)
+          if (sources[q2].layers[b2] == l)
+            return fail(MEM_ERR_ARG, "layer %d is bound to sources %d and %d", l, q2, q);
     }
     out[q].data = s.data;
     out[q].dtype = s.dtype;
@@ -568,7 +572,6 @@ static mem_status check_sources(const Map* m, int32_t n_sources, const mem_sourc
       if (m->cfg.layers[s.layers[b]].rule == MEM_RULE_CLASSMAX) out[q].has_classmax = 1;
     for (int b = 0; b < MEM_MAX_SOURCE_LAYERS; ++b) out[q].layers[b] = b < s.n_layers ? s.layers[b] : 0;
   }
-  (void)image;
   return MEM_OK;
 }
 
@@ -597,7 +600,7 @@ static mem_status run_points(Map* m, int nm, const int64_t* offsets, int64_t n, 
   job->xyz = xyz;
   job->n_maps = nm;
   job->n_src = n_src;
-  int acc = 8;  // record header
+  int acc = kSlotHdr;  // slot header
   for (int q = 0; q < n_src; ++q) {
     job->src[q] = src[q];
     job->src[q].acc_off = acc;
@@ -663,7 +666,7 @@ extern "C" mem_status mem_fuse_pointcloud(mem_map* mm, int64_t n, const float* x
   SrcDev src[MEM_MAX_SOURCES];
   mem_status s = check_sources(m, n_sources, sources, src, false);
   if (s != MEM_OK) return s;
-  return run_points(m, 1, nullptr, n, xyz, src, n_sources, T_map_sensor, false, (cudaStream_t)stream);
+  return run_points(m, 1, nullptr, n, xyz, src, n_sources, T_map_sensor, true, (cudaStream_t)stream);
 }
 
 extern "C" mem_status mem_fuse_pointcloud_batch(mem_map* mm, const int64_t* offsets, const float* xyz,

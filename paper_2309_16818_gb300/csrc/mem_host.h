@@ -51,7 +51,7 @@ struct Map {
 };
 
 // profile slots
-enum { kProfKey = 0, kProfDigits, kProfSort, kProfUnused, kProfFuseWindow, kProfFuseSpan,
+enum { kProfKey = 0, kProfDigits, kProfSort, kProfUnused3, kProfFuseSums, kProfFuseApply,
        kProfTime, kProfImage, kProfMove, kProfSlots };
 
 // Brackets a launch group with events when profiling is on.

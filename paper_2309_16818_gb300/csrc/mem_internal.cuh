@@ -18,7 +18,18 @@ constexpr int kMaxSrcLayers = MEM_MAX_SOURCE_LAYERS;
 constexpr u32 kFlagValid = 1u;               // bit 0: height valid
 constexpr u32 kSpinLimit = 1u << 22;         // bounded waits (x ~100 ns each)
 constexpr int kDevErrTimeout = 1;
+constexpr int kFuseTile = 128;               // sorted points per tile of the fuse kernels
+constexpr int kSlotHdr = 16;                 // words of a fuse slot before its channel sums
+// fuse slot header: sum w, sum w z, accepted, rejected (floats), then (bits)
+// cell key, points, begin/end bits, pre-call flags, height, variance,
+// accepted and rejected counts
+enum { kSlotKey = 4, kSlotN, kSlotBits, kSlotFl, kSlotH0, kSlotV0, kSlotNacc, kSlotNrej };
 
+// words of the fuse scratch for `cap` points: tile tables, then at most one
+// slot per point (every run piece of a tile holds at least one point)
+__host__ __device__ constexpr int64_t fuse_scratch_words(int64_t cap, int acc) {
+  return 2 * (cap / kFuseTile + 2) + cap * (int64_t)acc;
+}
 // Per-layer static description (device copy of mem_layer_desc + derived).
 struct LayerDev {
   int C;        // channels of the observations
@@ -48,8 +59,9 @@ struct MapDev {
   u32 *keys0, *keys1, *vals0, *vals1;
   u32* hist;        // [passes][radix] digit counts, then exclusive offsets
   u32* lookback;    // [passes][tiles][radix]
-  u32* counters;    // [0..3] tile counters per pass, [6] kept points
-  float* partial;   // [2 per 32-point window][acc] partial records of cells crossing windows
+  u32* counters;    // [0..3] tile counters per pass, [4] crossing cells, [5] touched cells,
+                    // [6] kept points, [7] [9] tile counters of the fuse kernels, [8] slots
+  float* partial;   // fuse scratch: tile slot bases, tile run counts, slots of acc words
   int64_t partial_cap;  // floats
   int* err;
   int64_t cap;      // point capacity of the scratch
@@ -83,7 +95,7 @@ struct PointJob {
   const MapCall* maps;     // [n_maps]
   int n_maps;
   int n_src;
-  int acc;  // floats per partial record: 8 header + per source C sums (+ max value, class)
+  int acc;  // words per fuse slot: kSlotHdr, then per source C sums (+ max value, class)
   SrcDev src[kMaxSources];
 };
 

@@ -29,8 +29,8 @@ constexpr int64_t kVals0 = kKeys1 + up(kMaxPts + 4);
 constexpr int64_t kVals1 = kVals0 + up(kMaxPts + 4);
 constexpr int64_t kHist = kVals1 + up(kMaxPts + 4);           // 4*1024 digits + 16 counters
 constexpr int64_t kLook = kHist + up(4 * 1024 + 16);           // 4 passes x tiles x 1024
-constexpr int64_t kPart = kLook + up(4 * kTiles * 1024);       // 2 records of 8 floats per window
-constexpr int64_t kErr = kPart + up(2 * (kMaxPts / 32 + 2) * 8);
+constexpr int64_t kPart = kLook + up(4 * kTiles * 1024);       // fuse tile tables + slots
+constexpr int64_t kErr = kPart + up(memk::fuse_scratch_words(kMaxPts, memk::kSlotHdr));
 constexpr int64_t kJob = kErr + up(1);
 struct JobBlock {
   memk::PointJob job;
@@ -39,7 +39,7 @@ struct JobBlock {
 constexpr int64_t kJobWords = up((sizeof(JobBlock) + 3) / 4);
 constexpr int64_t kWords = kJob + kJobWords;
 
-// every GPU that loads the library holds this array (about 5.3 MB) until exit
+// every GPU that loads the library holds this array (about 22 MB) until exit
 static __device__ __align__(256) u32 g_noalloc_scratch[kWords];
 
 std::mutex g_mu;
@@ -123,7 +123,7 @@ extern "C" mem_status mem_fuse_pointcloud_noalloc(const mem_map_config* cfg, con
   md.counters = md.hist + 4 * 1024;
   md.lookback = w + kLook;
   md.partial = (float*)(w + kPart);
-  md.partial_cap = 2 * (kMaxPts / 32 + 2) * 8;
+  md.partial_cap = memk::fuse_scratch_words(kMaxPts, memk::kSlotHdr);
   md.err = (int*)(w + kErr);
   md.cap = kMaxPts;
   md.cap_tiles = kTiles;
@@ -141,7 +141,7 @@ extern "C" mem_status mem_fuse_pointcloud_noalloc(const mem_map_config* cfg, con
   hj.job.maps = (const MapCall*)((char*)d_job + offsetof(JobBlock, mc));
   hj.job.n_maps = 1;
   hj.job.n_src = 0;
-  hj.job.acc = 8;
+  hj.job.acc = memk::kSlotHdr;
   for (int r = 0; r < 3; ++r)
     for (int k = 0; k < 3; ++k) hj.mc.R[r * 3 + k] = (float)T_map_sensor[r * 4 + k];
   hj.mc.t[0] = (float)(T_map_sensor[3] - origin_xy[0]);

@@ -3,13 +3,14 @@
 //
 //   k_points_key    transform, range filter and cell key of every point
 //                   (+ digit histograms of every radix pass)
-//   k_digit_scan    exclusive offsets of each digit
 //   k_onesweep      stable LSD radix-sort pass with decoupled look-back,
-//                   one per digit (keys = map * W*W + physical cell)
-//   k_fuse_window / per cell: outlier gate + Kalman height update, then every
-//   k_fuse_span     multi-modal layer's rule, as a reduce-by-key over 32-point
-//                   windows (no float atomics, fixed summation order, so the
-//                   results are run-to-run identical)
+//                   one per digit (keys = map * W*W + physical cell); each
+//                   CTA first scans the digit counts into global offsets
+//   k_fuse_sums     per tile of sorted points: outlier gate, then the sums of
+//                   every cell's quantities (a reduce-by-key in a fixed order)
+//   k_fuse_apply    per cell: Kalman height update, then every multi-modal
+//                   layer's rule (no float atomics, fixed summation order, so
+//                   the results are run-to-run identical)
 //
 // Every kernel reads its per-call parameters from the device-resident job, so
 // the sequence replays unchanged from a CUDA graph.
@@ -24,6 +25,7 @@ constexpr u32 kLbA = 1u << 30;                    // aggregate published
 constexpr u32 kLbP = 2u << 30;                    // inclusive prefix published
 constexpr u32 kLbFlags = 3u << 30;
 constexpr u32 kLbVal = (1u << 30) - 1;
+constexpr int kLookBack = 16;                     // predecessors read per look-back round
 
 __device__ __forceinline__ int find_map(const int64_t* __restrict__ off, int nm, int64_t i) {
   int lo = 0, hi = nm;
@@ -62,7 +64,8 @@ __global__ void __launch_bounds__(256) k_points_key(MapDev md, const PointJob* _
   const int64_t n4 = (n + 3) >> 2;
   MapCall mc = job->maps[0];
   int cur_b = 0;
-  u32 kept = 0;
+  u32 kept = 0, dropped = 0;
+  const int lane = threadIdx.x & 31;
   for (int64_t q = gtid; q < n4; q += gstride) {
     const int64_t i0 = q * 4;
     float p[12];
@@ -94,9 +97,13 @@ __global__ void __launch_bounds__(256) k_points_key(MapDev md, const PointJob* _
       const u32 key = e.keep ? (u32)b * md.W2 + phys_cell(md, mc, e.ix, e.iy) : md.sentinel;
       keys[k] = key;
       kept += e.keep ? 1u : 0u;
-      for (int ps = 0; ps < passes; ++ps)
-        atomicAdd(&shist[ps * RADIX + ((key >> (ps * RB)) & (RADIX - 1))], 1u);
+      dropped += e.keep ? 0u : 1u;
     }
+    // kept points' digits; dropped points (the sentinel key) are counted once per thread
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (i0 + k < n && keys[k] != md.sentinel)
+        for (int ps = 0; ps < passes; ++ps) atomicAdd(&shist[ps * RADIX + ((keys[k] >> (ps * RB)) & (RADIX - 1))], 1u);
     if (i0 + 4 <= n) {
       *reinterpret_cast<uint4*>(md.keys0 + i0) = make_uint4(keys[0], keys[1], keys[2], keys[3]);
     } else {
@@ -105,34 +112,17 @@ __global__ void __launch_bounds__(256) k_points_key(MapDev md, const PointJob* _
     }
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) kept += __shfl_xor_sync(0xffffffffu, kept, o);
-  if ((threadIdx.x & 31) == 0 && kept) atomicAdd(&shist[passes * RADIX], kept);
+  for (int o = 16; o > 0; o >>= 1) {
+    kept += __shfl_xor_sync(0xffffffffu, kept, o);
+    dropped += __shfl_xor_sync(0xffffffffu, dropped, o);
+  }
+  if (lane == 0 && kept) atomicAdd(&shist[passes * RADIX], kept);
+  if (lane == 0 && dropped)
+    for (int ps = 0; ps < passes; ++ps) atomicAdd(&shist[ps * RADIX + ((md.sentinel >> (ps * RB)) & (RADIX - 1))], dropped);
   __syncthreads();
   for (int i = threadIdx.x; i < passes * RADIX; i += blockDim.x)
     if (shist[i]) atomicAdd(&md.hist[i], shist[i]);
   if (threadIdx.x == 0 && shist[passes * RADIX]) atomicAdd(&md.counters[6], shist[passes * RADIX]);
-}
-
-// 2. digit counts -> exclusive digit offsets, for every pass (one block of 1024)
-__global__ void __launch_bounds__(1024) k_digit_scan(MapDev md, int passes, int radix) {
-  __shared__ u32 wsum[32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int p = 0; p < passes; ++p) {
-    u32* h = md.hist + p * radix;
-    u32 x = threadIdx.x < radix ? h[threadIdx.x] : 0u;
-    u32 inc = x;
-    for (int o = 1; o < 32; o <<= 1) {
-      u32 y = __shfl_up_sync(0xffffffffu, inc, o);
-      if (lane >= o) inc += y;
-    }
-    if (lane == 31) wsum[warp] = inc;
-    __syncthreads();
-    u32 base = 0;
-    for (int w = 0; w < warp; ++w) base += wsum[w];
-    __syncthreads();
-    if (threadIdx.x < radix) h[threadIdx.x] = base + inc - x;
-    __syncthreads();
-  }
 }
 
 // 3. one stable radix pass (onesweep: tiles taken in order from a counter,
@@ -150,6 +140,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(MapDev md, const Poin
   u32* scnt = svals + kTile;             // [RADIX]
   int* sstart = (int*)(scnt + RADIX);    // [RADIX]
   int* sgbase = sstart + RADIX;          // [RADIX]
+  u32* sgdig = (u32*)(sgbase + RADIX);   // [RADIX] exclusive offsets of the digits over all keys
   __shared__ int s_tile;
   __shared__ u32 s_wsum[WARPS];
 
@@ -160,10 +151,34 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(MapDev md, const Poin
   u32* __restrict__ kout = (pass & 1) ? md.keys0 : md.keys1;
   const u32* __restrict__ vin = (pass & 1) ? md.vals1 : md.vals0;
   u32* __restrict__ vout = (pass & 1) ? md.vals0 : md.vals1;
-  const u32* gdig = md.hist + pass * RADIX;
   u32* lb = md.lookback + (size_t)pass * md.cap_tiles * RADIX;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const u32 lt = (1u << lane) - 1u;
+  // exclusive offsets of this pass's digits from the key kernel's counts
+  {
+    u32 loc[RPT];
+    u32 tsum = 0;
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      loc[r] = md.hist[pass * RADIX + threadIdx.x * RPT + r];
+      tsum += loc[r];
+    }
+    u32 inc = tsum;
+    for (int o = 1; o < 32; o <<= 1) {
+      const u32 y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    if (lane == 31) s_wsum[warp] = inc;
+    __syncthreads();
+    u32 run = inc - tsum;
+    for (int w = 0; w < warp; ++w) run += s_wsum[w];
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      sgdig[threadIdx.x * RPT + r] = run;
+      run += loc[r];
+    }
+    __syncthreads();
+  }
 
   for (;;) {
     if (threadIdx.x == 0) s_tile = atomicAdd(&md.counters[pass], 1);
@@ -234,6 +249,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(MapDev md, const Poin
         run += loc[r];
       }
     }
+    __syncthreads();  // sstart is read below by the thread owning each digit
     // publish this tile's counts, then look back for the exclusive prefix
     for (int d = threadIdx.x; d < RADIX; d += kSortThreads) {
       const u32 c = scnt[d];
@@ -243,18 +259,19 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(MapDev md, const Poin
         st_relaxed(me, kLbP | c);
       } else {
         st_relaxed(me, kLbA | c);
-        // walk back 8 predecessors per round: add aggregates until an
-        // inclusive prefix is found; wait (bounded) where one is not ready
+        // walk back kLookBack predecessors per round: add aggregates until
+        // an inclusive prefix is found; wait (bounded) where one is not ready
         int k = tile - 1;
         u32 spins = 0;
         for (;;) {
-          u32 v[8];
+          u32 v[kLookBack];
 #pragma unroll
-          for (int j = 0; j < 8; ++j) v[j] = (k - j >= 0) ? ld_relaxed(lb + (size_t)(k - j) * RADIX + d) : kLbP;
-          int adv = 8;
+          for (int j = 0; j < kLookBack; ++j)
+            v[j] = (k - j >= 0) ? ld_relaxed(lb + (size_t)(k - j) * RADIX + d) : kLbP;
+          int adv = kLookBack;
           bool fin = false, wait = false;
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
+          for (int j = 0; j < kLookBack; ++j) {
             if (!fin && !wait) {
               const u32 f = v[j] & kLbFlags;
               if (f == 0) {
@@ -278,7 +295,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(MapDev md, const Poin
         }
         st_relaxed(me, kLbP | ((excl + c) & kLbVal));
       }
-      sgbase[d] = (int)(gdig[d] + excl) - sstart[d];
+      sgbase[d] = (int)(sgdig[d] + excl) - sstart[d];
     }
     __syncthreads();
     // stage the tile in digit order, then write runs of equal digits
@@ -306,192 +323,53 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(MapDev md, const Poin
 }
 
 // ---------------------------------------------------------------------------
-// 4. per-cell fusion, as a reduce-by-key over the sorted points
+// 4. per-cell fusion, as a reduce-by-key over tiles of sorted points
 //
-// k_fuse_window: one warp per window of 32 consecutive sorted points, one
-//   lane per point. Every lane issues its loads at once (point, source rows,
-//   its cell's prior state), then the per-cell sums and maxima are formed by
-//   segmented scans across the lanes. A cell whose points all lie in the
-//   window is finished right there by the lane holding its last point. A cell
-//   that crosses a window boundary leaves one partial record per window it
-//   touches: slot 1 of the window where it starts, slot 0 of every later
-//   window (flagged on the window where it ends).
-// k_fuse_span: one warp per window whose slot 1 holds a crossing cell adds
-//   the cell's records in window order and applies the rules (lane c owns
-//   channel c).
-// The float32 summation order only depends on the sorted order, which is
+// The sorted points are cut into tiles of kFuseTile; the points of one cell
+// form one run of the sorted order, and a run may cross tile boundaries.
+//
+// k_fuse_sums: one CTA per tile (persistent, tiles taken from a counter).
+//   Every quantity summed per cell is a column of a stage in shared memory
+//   with one row per point: the four height sums (after the outlier gate
+//   against the pre-call state), then every source's channels, then, for a
+//   source bound to a class-max layer, the point's largest channel value and
+//   its channel. Up to kQ columns are staged at once (a round); a thread
+//   walks one column over a fixed segment of the tile's points in point
+//   order, and the pieces of a run that crosses segments are added in
+//   segment order. Each run piece of the tile leaves one slot: its sums,
+//   its cell, its pre-call state, and whether the run begins / ends in the
+//   tile.
+// k_fuse_apply: one CTA per tile again. The tile completes every run that
+//   begins in it: a run that continues past the tile adds the slots of the
+//   following tiles' first runs, in tile order. Then the Kalman height update
+//   and every layer's rule, then class max, Gaussian variances and flags.
+// The float32 summation order depends only on the sorted order, which is
 // deterministic: results are identical from run to run.
 
-// record header (floats): sum w, sum w z, accepted (bits), rejected (bits),
-// flag (bits), cell key (bits), 2 unused
-constexpr int kRecHdr = 8;
-constexpr u32 kRecStart = 1u;  // slot 1: a crossing cell starts in this window
-constexpr u32 kRecMore = 1u;   // slot 0: the cell continues past this window
-constexpr u32 kRecLast = 2u;   // slot 0: the cell ends in this window
+constexpr int kFT = kFuseTile;  // threads of a fuse CTA = sorted points per tile
+constexpr int kQ = 32;          // stage columns per round
+constexpr int kQS = kQ + 1;     // row stride of the stage (odd: conflict-free columns)
+constexpr int kSegMax = 32;     // segments of a tile per walk
+constexpr int kStageU = 6;      // staging chunks in flight per thread
+constexpr int kApplyU = 4;      // rule tasks in flight per thread
+constexpr u32 kBitHead = 1u;    // slot bits: the run begins in the tile
+constexpr u32 kBitEnd = 2u;     //            the run ends in the tile
+constexpr int kChArgV = -1;     // column of a source's arg-max value
+constexpr int kChArgI = -2;     // column of a source's arg-max channel
 
-// map-frame z and measurement variance of a point already known to be kept
-// (the same operation sequence as eval_point, so the same bits)
-__device__ __forceinline__ void eval_zvm(const MapDev& md, const MapCall& mc, float xs, float ys,
-                                         float zs, float& z, float& vm) {
-  float r2 = __fmaf_rn(xs, xs, __fmaf_rn(ys, ys, __fmul_rn(zs, zs)));
-  float rs = __fsqrt_rn(r2);
-  z = __fmaf_rn(mc.R[6], xs, __fmaf_rn(mc.R[7], ys, __fmaf_rn(mc.R[8], zs, mc.t[2])));
-  float sm = __fmaf_rn(md.sigma1, rs, md.sigma0);
-  vm = __fmul_rn(sm, sm);
+// fuse scratch: [tile_base | tile_runs | slots]
+__device__ __forceinline__ u32* fz_tile_base(const MapDev& md) { return (u32*)md.partial; }
+__device__ __forceinline__ u32* fz_tile_runs(const MapDev& md) {
+  return (u32*)md.partial + (md.cap / kFT + 2);
 }
-
-struct HeightAcc {
-  float sw, swz;
-  u32 na, nr;
-};
-
-// Kalman height update in information form (float32) + cumulative counts.
-__device__ __forceinline__ void height_update(const MapDev& md, int64_t g, u32& fl, float h0, float v0,
-                                              const HeightAcc& a) {
-  float h = h0, v = v0;
-  if (a.na > 0) {
-    if (fl & kFlagValid) {
-      const float P = __frcp_rn(v0) + a.sw;
-      h = (h0 * __frcp_rn(v0) + a.swz) * __frcp_rn(P);
-      v = __frcp_rn(P);
-    } else {
-      h = a.swz * __frcp_rn(a.sw);
-      v = __frcp_rn(a.sw);
-      fl |= kFlagValid;
-    }
-  }
-  if (a.nr > 0 && md.outlier_var != 0.f) v = fmaf(md.outlier_var, (float)a.nr, v);
-  md.h[g] = h;
-  md.var[g] = v;
-  md.n_acc[g] += a.na;
-  md.n_rej[g] += a.nr;
+__device__ __forceinline__ float* fz_slot(const MapDev& md, int acc, int64_t slot) {
+  return md.partial + 2 * (md.cap / kFT + 2) + slot * acc;
 }
 
-// coefficients of layer l for one cell
-__device__ __forceinline__ RuleCoef layer_coef(const MapDev& md, int l, int64_t g, u32 fl, float N, float rN) {
-  const LayerDev& L = md.L[l];
-  const bool obs = fl & (2u << l);
-  const float s02 = (L.rule == MEM_RULE_GAUSS && obs) ? L.gvar[g] : 0.f;
-  return rule_coef(L, N, rN, obs, s02);
-}
+// slot offset of global column gc (height sums first, then the header)
+__device__ __forceinline__ int slot_off(int gc) { return gc < 4 ? gc : gc + (kSlotHdr - 4); }
 
-// class-max and Gaussian-variance writes after all channels of a source
-__device__ __forceinline__ void finish_source(const MapDev& md, const SrcDev& src, int64_t g, u32& fl,
-                                              float N, float rN, float best, int bid) {
-  for (int b = 0; b < src.n_layers; ++b) {
-    const int l = src.layers[b];
-    const LayerDev& L = md.L[l];
-    if (L.rule == MEM_RULE_CLASSMAX) {
-      float* d = (float*)L.data + g * 2;
-      d[0] = (float)bid;
-      d[1] = best;
-    } else if (L.rule == MEM_RULE_GAUSS) {
-      L.gvar[g] = layer_coef(md, l, g, fl, N, rN).var_new;
-    }
-  }
-  for (int b = 0; b < src.n_layers; ++b) fl |= 2u << src.layers[b];
-}
-
-// old values of four channels of a layer (vector access when possible)
-__device__ __forceinline__ void ld_old4(const LayerDev& L, int64_t off, int nc, float o[4]) {
-  if (nc == 4 && (off & 3) == 0 && L.dtype == MEM_F32) {
-    const float4 q = *reinterpret_cast<const float4*>((const float*)L.data + off);
-    o[0] = q.x; o[1] = q.y; o[2] = q.z; o[3] = q.w;
-    return;
-  }
-  if (nc == 4 && (off & 3) == 0 && L.dtype == MEM_BF16) {
-    const uint2 q = *reinterpret_cast<const uint2*>((const __nv_bfloat16*)L.data + off);
-    const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&q.x));
-    const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&q.y));
-    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
-    return;
-  }
-#pragma unroll
-  for (int k = 0; k < 4; ++k) o[k] = k < nc ? ld_layer(L, off + k) : 0.f;
-}
-
-__device__ __forceinline__ void st_new4(const LayerDev& L, int64_t off, int nc, const float n[4]) {
-  if (nc == 4 && (off & 3) == 0 && L.dtype == MEM_F32) {
-    *reinterpret_cast<float4*>((float*)L.data + off) = make_float4(n[0], n[1], n[2], n[3]);
-    return;
-  }
-  if (nc == 4 && (off & 3) == 0 && L.dtype == MEM_BF16) {
-    __nv_bfloat162 a = __floats2bfloat162_rn(n[0], n[1]), b = __floats2bfloat162_rn(n[2], n[3]);
-    uint2 q;
-    q.x = *reinterpret_cast<u32*>(&a);
-    q.y = *reinterpret_cast<u32*>(&b);
-    *reinterpret_cast<uint2*>((__nv_bfloat16*)L.data + off) = q;
-    return;
-  }
-  for (int k = 0; k < nc; ++k) st_layer(L, off + k, n[k]);
-}
-
-// segmented inclusive scans over the lanes of a warp: `use[s]` says whether
-// the lane 2^s positions down belongs to the same run
-__device__ __forceinline__ float seg_sum(float v, const bool use[5]) {
-#pragma unroll
-  for (int s = 0; s < 5; ++s) {
-    const float y = __shfl_up_sync(0xffffffffu, v, 1 << s);
-    if (use[s]) v += y;
-  }
-  return v;
-}
-__device__ __forceinline__ u32 seg_sum_u(u32 v, const bool use[5]) {
-#pragma unroll
-  for (int s = 0; s < 5; ++s) {
-    const u32 y = __shfl_up_sync(0xffffffffu, v, 1 << s);
-    if (use[s]) v += y;
-  }
-  return v;
-}
-__device__ __forceinline__ float seg_max(float v, const bool use[5]) {
-#pragma unroll
-  for (int s = 0; s < 5; ++s) {
-    const float y = __shfl_up_sync(0xffffffffu, v, 1 << s);
-    if (use[s]) v = fmaxf(v, y);
-  }
-  return v;
-}
-
-constexpr int kPre = 4;   // layers per source whose coefficients stay in registers
-constexpr int kBlk = 16;  // channels per block in the window kernel
-
-// typed access to four consecutive stored values
-template <int DT>
-__device__ __forceinline__ void ld4t(const void* base, int64_t off, float o[4]) {
-  if (DT == MEM_F32) {
-    const float4 q = *reinterpret_cast<const float4*>((const float*)base + off);
-    o[0] = q.x; o[1] = q.y; o[2] = q.z; o[3] = q.w;
-  } else if (DT == MEM_BF16) {
-    const uint2 q = *reinterpret_cast<const uint2*>((const __nv_bfloat16*)base + off);
-    const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&q.x));
-    const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&q.y));
-    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
-  } else {
-    const uint2 q = *reinterpret_cast<const uint2*>((const __half*)base + off);
-    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&q.x));
-    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&q.y));
-    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
-  }
-}
-template <int DT>
-__device__ __forceinline__ void st4t(void* base, int64_t off, const float n[4]) {
-  if (DT == MEM_F32) {
-    *reinterpret_cast<float4*>((float*)base + off) = make_float4(n[0], n[1], n[2], n[3]);
-  } else if (DT == MEM_BF16) {
-    __nv_bfloat162 a = __floats2bfloat162_rn(n[0], n[1]), b = __floats2bfloat162_rn(n[2], n[3]);
-    uint2 q;
-    q.x = *reinterpret_cast<u32*>(&a);
-    q.y = *reinterpret_cast<u32*>(&b);
-    *reinterpret_cast<uint2*>((__nv_bfloat16*)base + off) = q;
-  } else {
-    __half2 a = __floats2half2_rn(n[0], n[1]), b = __floats2half2_rn(n[2], n[3]);
-    uint2 q;
-    q.x = *reinterpret_cast<u32*>(&a);
-    q.y = *reinterpret_cast<u32*>(&b);
-    *reinterpret_cast<uint2*>((__half*)base + off) = q;
-  }
-}
+// typed access to one stored value
 template <int DT>
 __device__ __forceinline__ float ld1t(const void* base, int64_t off) {
   if (DT == MEM_F32) return ((const float*)base)[off];
@@ -504,7 +382,6 @@ __device__ __forceinline__ void st1t(void* base, int64_t off, float v) {
   else if (DT == MEM_BF16) ((__nv_bfloat16*)base)[off] = __float2bfloat16_rn(v);
   else ((__half*)base)[off] = __float2half_rn(v);
 }
-
 template <int RULE>
 __device__ __forceinline__ float rule_value_t(const LayerDev& L, float old, float S, const RuleCoef& r) {
   if (RULE == MEM_RULE_LATEST) return S * r.a;
@@ -516,326 +393,651 @@ __device__ __forceinline__ float rule_value_t(const LayerDev& L, float old, floa
   return (r.obs ? old : L.alpha0) + S;  // DIRICHLET
 }
 
-// One layer's rule over a block of nb <= kBlk channels starting at `off`:
-// every old value of the block is loaded before any new value is stored.
-template <int RULE, int DT>
-__device__ __forceinline__ void apply_block_t(const LayerDev& L, int64_t off, const float S[kBlk], int nb,
-                                              const RuleCoef& r) {
-  const bool need = RULE != MEM_RULE_LATEST && r.obs;
-  float o[kBlk];
-  const bool vec = (off & 3) == 0;
-#pragma unroll
-  for (int j = 0; j < kBlk / 4; ++j) {
-    o[4 * j] = o[4 * j + 1] = o[4 * j + 2] = o[4 * j + 3] = 0.f;
-    if (need && 4 * j < nb) {
-      if (vec && 4 * j + 4 <= nb) {
-        ld4t<DT>(L.data, off + 4 * j, &o[4 * j]);
+struct __align__(16) ChunkDesc {  // up to four consecutive channels of one source staged together
+  const void* data;
+  int C, ch0;       // row length, first channel
+  int col, n;       // first stage column, channels
+  int dtype, vec;   // storage, 16-byte aligned rows
+  int am;           // arg-max value column of the source (-1: none); bit 30: last chunk
+  int pad;          // source
+  int unused[2];
+};
+
+struct SumSmem {
+  u32 key[kFT + 2];  // key[i + 1]: point i; key[0]: the point before the tile; key[np + 1]: after it
+  u32 idx[kFT];
+  int pinf[kFT];     // point: run << 1 | 1 if it is the last point of its run in the tile
+  int rstart[kFT + 1];
+  u32 fl[kFT];       // per run: pre-call flags, height, variance (the gate's state)
+  float h0[kFT], v0[kFT];
+  float stage[kFT * kQS];
+  float2 hp[kFT], tp[kFT];  // segment pieces of runs that cross segment boundaries
+  int col_src[kQ];          // per column of the round: source (-1: height sums)
+  int col_ch[kQ];           // channel, kChArgV / kChArgI, or height sum 0..3
+  ChunkDesc ck[kQ];
+  int n_ck;
+  SrcDev src[kMaxSources];
+  MapCall mc0;
+  u32 wcnt[kFT / 32];
+  u32 endbits[kFT / 32];  // bit i: point i is the last point of its run in the tile
+  int tile;
+  u32 base;
+  int fallback;           // an arg-max pair of the round needs channels of an earlier round
+};
+
+// map-frame z and measurement variance of a point already known to be kept
+// (the same operation sequence as eval_point, so the same bits)
+__device__ __forceinline__ void eval_zvm(const MapDev& md, const MapCall& mc, float xs, float ys,
+                                         float zs, float& z, float& vm) {
+  float r2 = __fmaf_rn(xs, xs, __fmaf_rn(ys, ys, __fmul_rn(zs, zs)));
+  float rs = __fsqrt_rn(r2);
+  z = __fmaf_rn(mc.R[6], xs, __fmaf_rn(mc.R[7], ys, __fmaf_rn(mc.R[8], zs, mc.t[2])));
+  float sm = __fmaf_rn(md.sigma1, rs, md.sigma0);
+  vm = __fmul_rn(sm, sm);
+}
+
+__device__ __forceinline__ float2 cm_comb(float2 a, float2 b) {  // larger value, smaller channel on ties
+  return (b.x > a.x || (b.x == a.x && __float_as_int(b.y) < __float_as_int(a.y))) ? b : a;
+}
+
+// source and channel of global column gc >= 4
+__device__ __forceinline__ void col_ident(const SrcDev* src, int n_src, int gc, int& q, int& ch) {
+  const int o = slot_off(gc);
+  q = 0;
+  for (int k = 1; k < n_src; ++k)
+    if (src[k].acc_off <= o) q = k;
+  const int c = o - src[q].acc_off;
+  ch = c < src[q].C ? c : (c == src[q].C ? kChArgV : kChArgI);
+}
+
+// end of the round that starts at column r0 (an arg-max pair never splits)
+__device__ __forceinline__ int round_end(const SrcDev* src, int n_src, int r0, int G) {
+  int re = min(r0 + kQ, G);
+  if (re < G && re - 1 >= 4) {
+    int q, ch;
+    col_ident(src, n_src, re - 1, q, ch);
+    if (ch == kChArgV) --re;
+  }
+  return re;
+}
+
+// Column table of the round [r0, r0 + nr), then (thread 0) its staging chunks.
+__device__ __forceinline__ void build_columns(SumSmem& s, int n_src, int r0, int nr) {
+  if (threadIdx.x < nr) {
+    int q = -1, ch = r0 + threadIdx.x;
+    if (r0 + threadIdx.x >= 4) col_ident(s.src, n_src, r0 + threadIdx.x, q, ch);
+    s.col_src[threadIdx.x] = q;
+    s.col_ch[threadIdx.x] = ch;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int n = 0;
+    for (int c = 0; c < nr; ++c) {
+      const int q = s.col_src[c], ch = s.col_ch[c];
+      if (q < 0 || ch < 0) continue;
+      const bool extend = n > 0 && s.ck[n - 1].n < 4 && (ch & 3) != 0 && s.col_src[c - 1] == q &&
+                          s.col_ch[c - 1] == ch - 1 && s.ck[n - 1].col + s.ck[n - 1].n == c;
+      if (extend) {
+        ++s.ck[n - 1].n;
       } else {
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-          if (4 * j + k < nb) o[4 * j + k] = ld1t<DT>(L.data, off + 4 * j + k);
+        ChunkDesc& d = s.ck[n++];
+        d.data = s.src[q].data;
+        d.C = s.src[q].C;
+        d.ch0 = ch;
+        d.col = c;
+        d.n = 1;
+        d.dtype = s.src[q].dtype;
+        d.vec = s.src[q].vec_ok;
+        d.pad = q;
       }
     }
-  }
-#pragma unroll
-  for (int j = 0; j < kBlk / 4; ++j) {
-    if (4 * j < nb) {
-      float n[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) n[k] = rule_value_t<RULE>(L, o[4 * j + k], S[4 * j + k], r);
-      if (vec && 4 * j + 4 <= nb) {
-        st4t<DT>(L.data, off + 4 * j, n);
-      } else {
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-          if (4 * j + k < nb) st1t<DT>(L.data, off + 4 * j + k, n[k]);
-      }
+    s.n_ck = n;
+    s.fallback = 0;
+    for (int c = 0; c < nr; ++c)
+      if (s.col_ch[c] == kChArgV && slot_off(r0) > s.src[s.col_src[c]].acc_off) s.fallback = 1;
+    // a source whose channels and arg-max pair are all in the round gets its
+    // per-point arg-max while it is staged
+    for (int k = 0; k < n; ++k) {
+      const int q = s.ck[k].pad;
+      const int first = s.ck[k].col - s.ck[k].ch0;  // column of channel 0
+      const int av = first + s.src[q].C;            // arg-max value column
+      const bool ok = s.src[q].has_classmax && first >= 0 && av + 1 < nr;
+      const bool last = k + 1 == n || s.ck[k + 1].pad != q;
+      s.ck[k].am = ok ? (av | (last ? (1 << 30) : 0)) : -1;
     }
   }
 }
 
-__device__ __forceinline__ void apply_block(const LayerDev& L, int64_t off, const float S[kBlk], int nb,
-                                              const RuleCoef& r) {
-#define MEM_AB(R, D) \
-  case R * 4 + D: apply_block_t<R, D>(L, off, S, nb, r); break;
-  switch (L.rule * 4 + L.dtype) {
-    MEM_AB(MEM_RULE_LATEST, MEM_F32) MEM_AB(MEM_RULE_LATEST, MEM_BF16) MEM_AB(MEM_RULE_LATEST, MEM_F16)
-    MEM_AB(MEM_RULE_EXPAVG, MEM_F32) MEM_AB(MEM_RULE_EXPAVG, MEM_BF16) MEM_AB(MEM_RULE_EXPAVG, MEM_F16)
-    MEM_AB(MEM_RULE_GAUSS, MEM_F32) MEM_AB(MEM_RULE_GAUSS, MEM_BF16) MEM_AB(MEM_RULE_GAUSS, MEM_F16)
-    MEM_AB(MEM_RULE_DIRICHLET, MEM_F32)
-    default: break;
+// four consecutive channels of a row (fewer at the end of the row)
+__device__ __forceinline__ void ld_chunk(const ChunkDesc& d, int64_t row, float v[4]) {
+  const int64_t off = row * d.C + d.ch0;
+  if (d.n == 4 && d.vec && (off & 3) == 0) {
+    if (d.dtype == MEM_F32) {
+      const float4 q = __ldg((const float4*)((const float*)d.data + off));
+      v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+      return;
+    }
+    if (d.dtype == MEM_BF16 || d.dtype == MEM_F16) {
+      const uint2 q = __ldg((const uint2*)((const uint16_t*)d.data + off));
+      if (d.dtype == MEM_BF16) {
+        const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&q.x));
+        const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&q.y));
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+      } else {
+        const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&q.x));
+        const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&q.y));
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+      }
+      return;
+    }
   }
-#undef MEM_AB
+#pragma unroll
+  for (int w = 0; w < 4; ++w) v[w] = w < d.n ? ld_any(d.data, d.dtype, off + w) : 0.f;
 }
 
-__global__ void __launch_bounds__(256) k_fuse_window(MapDev md, const PointJob* __restrict__ job,
-                                                     int sorted1) {
+__global__ void __launch_bounds__(kFT, 6) k_fuse_sums(MapDev md, const PointJob* __restrict__ job,
+                                                      int sorted1) {
+  extern __shared__ __align__(16) unsigned char fz_raw[];
+  SumSmem& s = *reinterpret_cast<SumSmem*>(fz_raw);
   const u32* __restrict__ sk = sorted1 ? md.keys1 : md.keys0;
   const u32* __restrict__ sv = sorted1 ? md.vals1 : md.vals0;
   const int64_t n_kept = *(volatile u32*)&md.counters[6];
-  const float* __restrict__ xyz = job->xyz;
+  const int n_tiles = (int)((n_kept + kFT - 1) / kFT);
   const int n_src = job->n_src;
   const int acc = job->acc;
-  float* __restrict__ part = md.partial;
-  const int lane = threadIdx.x & 31;
-  const u32 lt = (1u << lane) - 1u;
-  const int64_t n_win = (n_kept + 31) >> 5;
-  const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < n_win; w += wstride) {
-    const int64_t p = w * 32 + lane;
-    const bool active = p < n_kept;
-    const u32 key = active ? sk[p] : 0xffffffffu;
-    const u32 idx = active ? sv[p] : 0u;
-    // neighbours (lane 0 / lane 31 look across the window edge)
-    u32 prev = __shfl_up_sync(0xffffffffu, key, 1);
-    u32 next = __shfl_down_sync(0xffffffffu, key, 1);
-    if (lane == 0) prev = p > 0 ? sk[p - 1] : 0xfffffffeu;
-    if (lane == 31) next = (p + 1 < n_kept) ? sk[p + 1] : 0xfffffffeu;
-    const bool ghead = active && prev != key;                 // first point of its cell
-    const bool gend = active && next != key;                  // last point of its cell
-    const bool lhead = active && (lane == 0 || prev != key);  // first point of the run in this window
-    const bool lend = active && (lane == 31 || next != key);  // last point of the run in this window
-    const u32 heads = __ballot_sync(0xffffffffu, lhead);
-    const int rs = 31 - __clz(heads & (lt | (1u << lane)));  // run start lane
-    bool use[5];
+  const int G = acc - (kSlotHdr - 4);  // global columns
+  const float* __restrict__ xyz = job->xyz;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  if (t < n_src) s.src[t] = job->src[t];
+  if (t == 0) s.mc0 = job->maps[0];
+  __syncthreads();
+  const bool one_round = round_end(s.src, n_src, 0, G) == G;
+  if (one_round) build_columns(s, n_src, 0, G);
+  for (;;) {
+    __syncthreads();  // the previous tile is done with the shared arrays
+    if (t == 0) s.tile = atomicAdd(&md.counters[7], 1);
+    __syncthreads();
+    const int tile = s.tile;
+    if (tile >= n_tiles) break;
+    const int64_t p0 = (int64_t)tile * kFT;
+    const int np = (int)min((int64_t)kFT, n_kept - p0);
+    // A. keys, point indices, runs
+    if (t < np) {
+      s.key[t + 1] = sk[p0 + t];
+      s.idx[t] = sv[p0 + t];
+    }
+    if (t == 0) s.key[0] = p0 > 0 ? sk[p0 - 1] : 0xfffffffeu;
+    if (t == 32) s.key[np + 1] = (p0 + np < n_kept) ? sk[p0 + np] : 0xfffffffeu;
+    __syncthreads();
+    const bool hd = t < np && (t == 0 || s.key[t] != s.key[t + 1]);
+    const bool ed = t < np && (t == np - 1 || s.key[t + 1] != s.key[t + 2]);
+    const u32 bal = __ballot_sync(0xffffffffu, hd);
+    const u32 ebal = __ballot_sync(0xffffffffu, ed);
+    if (lane == 0) {
+      s.wcnt[warp] = __popc(bal);
+      s.endbits[warp] = ebal;
+    }
+    __syncthreads();
+    int nruns = 0, rbase = 0;
 #pragma unroll
-    for (int s = 0; s < 5; ++s) use[s] = lane - (1 << s) >= rs;
-    const int run_ghead = __shfl_sync(0xffffffffu, (int)ghead, rs & 31);  // all lanes take part
-    const int lane0_ghead = __shfl_sync(0xffffffffu, (int)ghead, 0);
-    const bool complete = lend && gend && run_ghead != 0;
-    const bool partial = lend && !complete;
-    const bool from_before = rs == 0 && lane0_ghead == 0;  // run entered from the previous window
-    // this lane's cell
-    const u32 b = md.n_maps > 1 ? key / md.W2 : 0u;
-    const MapCall& mc = job->maps[active ? b : 0u];
-    const int64_t g = active ? key : 0;
-    u32 fl = active ? md.flags[g] : 0u;
-    const float h0 = active ? md.h[g] : 0.f, v0 = active ? md.var[g] : 0.f;
-    // height contribution of this point
-    HeightAcc a = {0.f, 0.f, 0u, 0u};
-    if (active) {
-      float z, vm;
-      eval_zvm(md, mc, __ldg(xyz + 3 * (int64_t)idx), __ldg(xyz + 3 * (int64_t)idx + 1),
-               __ldg(xyz + 3 * (int64_t)idx + 2), z, vm);
-      if ((fl & kFlagValid) && gate_reject(z, h0, v0, vm, md.lam2)) {
-        a.nr = 1;
-      } else {
-        a.na = 1;
-        a.sw = __frcp_rn(vm);
-        a.swz = z * a.sw;
+    for (int w = 0; w < kFT / 32; ++w) {
+      const int cw = (int)s.wcnt[w];
+      rbase += w < warp ? cw : 0;
+      nruns += cw;
+    }
+    const int myrun = rbase + __popc(bal & ((2u << lane) - 1u)) - 1;
+    if (t < np) s.pinf[t] = (myrun << 1) | (ed ? 1 : 0);
+    if (hd) s.rstart[myrun] = t;
+    if (t == 0) {
+      s.rstart[nruns] = np;
+      s.base = atomicAdd(&md.counters[8], (u32)nruns);
+    }
+    __syncthreads();
+    const u32 base = s.base;
+    if (t == 0) {
+      fz_tile_base(md)[tile] = base;
+      fz_tile_runs(md)[tile] = (u32)nruns;
+    }
+    // B. pre-call state of every run's cell into the slot header (and the
+    //    gate's part to shared memory), coordinates of every point
+    if (t < nruns) {
+      const int i0 = s.rstart[t], i1 = s.rstart[t + 1];
+      const u32 g = s.key[i0 + 1];
+      const u32 fl = md.flags[g];
+      const float h0 = md.h[g], v0 = md.var[g];
+      const u32 na = md.n_acc[g], nr = md.n_rej[g];
+      s.fl[t] = fl;
+      s.h0[t] = h0;
+      s.v0[t] = v0;
+      float* hdr = fz_slot(md, acc, base + t);
+      const u32 bits = (i0 > 0 || s.key[0] != s.key[1] ? kBitHead : 0u) |
+                       (i1 < np || s.key[np] != s.key[np + 1] ? kBitEnd : 0u);
+      hdr[kSlotKey] = __uint_as_float(g);
+      hdr[kSlotN] = __uint_as_float((u32)(i1 - i0));
+      hdr[kSlotBits] = __uint_as_float(bits);
+      hdr[kSlotFl] = __uint_as_float(fl);
+      hdr[kSlotH0] = h0;
+      hdr[kSlotV0] = v0;
+      hdr[kSlotNacc] = __uint_as_float(na);
+      hdr[kSlotNrej] = __uint_as_float(nr);
+    }
+    float xs = 0.f, ys = 0.f, zs = 0.f;
+    if (t < np) {
+      const int64_t id = s.idx[t];
+      xs = __ldg(xyz + 3 * id);
+      ys = __ldg(xyz + 3 * id + 1);
+      zs = __ldg(xyz + 3 * id + 2);
+    }
+    // C. rounds of at most kQ columns
+    for (int r0 = 0; r0 < G;) {
+      const int re = one_round ? G : round_end(s.src, n_src, r0, G);
+      const int nr = re - r0;
+      if (!one_round) {
+        __syncthreads();  // the previous round is done with the column tables
+        build_columns(s, n_src, r0, nr);
+        __syncthreads();
       }
-    }
-    a.sw = seg_sum(a.sw, use);
-    a.swz = seg_sum(a.swz, use);
-    a.na = seg_sum_u(a.na, use);
-    a.nr = seg_sum_u(a.nr, use);
-    float* rec = part + ((w * 2 + (from_before ? 0 : 1)) * (int64_t)acc);
-    if (complete) height_update(md, g, fl, h0, v0, a);
-    if (partial) {
-      rec[0] = a.sw;
-      rec[1] = a.swz;
-      rec[2] = __uint_as_float(a.na);
-      rec[3] = __uint_as_float(a.nr);
-      rec[4] = __uint_as_float(from_before ? (gend ? kRecLast : kRecMore) : kRecStart);
-      rec[5] = __uint_as_float(key);
-    }
-    // slot 1 of every window says whether a crossing cell starts here
-    if (lane == 31) {
-      const bool starts = partial && !from_before;
-      if (!starts) part[(w * 2 + 1) * (int64_t)acc + 4] = __uint_as_float(0u);
-    }
-    const float N = (float)(lane - rs + 1), rN = __frcp_rn(N);
-    for (int q = 0; q < n_src; ++q) {
-      const SrcDev& src = job->src[q];
-      // this point's largest class probability (smallest class on ties)
-      float pbest = -INFINITY;
-      int pbid = 0x7fffffff;
-      RuleCoef co[kPre];
+      // stage the source channels of the round: thread = point, kStageU
+      // chunks in flight before their stores; a source bound to a class-max
+      // layer gets the point's arg-max on the way
+      if (t < np) {
+        const int nck = s.n_ck;
+        const int64_t row_i = s.idx[t];
+        float* srow = s.stage + t * kQS;
+        float pb = -INFINITY;
+        int pi = 0x7fffffff;
+        for (int j0 = 0; j0 < nck; j0 += kStageU) {
+          float v[kStageU][4];
 #pragma unroll
-      for (int bb = 0; bb < kPre; ++bb) {
-        co[bb].a = co[bb].b = co[bb].var_new = 0.f;
-        co[bb].obs = false;
-        if (complete && bb < src.n_layers) co[bb] = layer_coef(md, src.layers[bb], g, fl, N, rN);
-      }
-      // channels in blocks of 16: loads, per-point arg-max, segmented sums,
-      // then each bound layer applies its rule to the whole block (rule and
-      // storage type resolved once per layer and block)
-      for (int cb = 0; cb < src.C; cb += kBlk) {
-        const int nb = min(kBlk, src.C - cb);
-        float v[kBlk];
+          for (int u = 0; u < kStageU; ++u)
+            if (j0 + u < nck) ld_chunk(s.ck[j0 + u], row_i, v[u]);
 #pragma unroll
-        for (int j = 0; j < kBlk / 4; ++j) {
-          v[4 * j] = v[4 * j + 1] = v[4 * j + 2] = v[4 * j + 3] = 0.f;
-          if (active && 4 * j < nb) ld_src4(src, idx, cb + 4 * j, &v[4 * j]);
-        }
-        if (src.has_classmax && active) {
+          for (int u = 0; u < kStageU; ++u) {
+            if (j0 + u < nck) {
+              const ChunkDesc& d = s.ck[j0 + u];
+              const int am = d.am;
 #pragma unroll
-          for (int k = 0; k < kBlk; ++k)
-            if (k < nb && v[k] > pbest) {
-              pbest = v[k];
-              pbid = cb + k;
+              for (int w = 0; w < 4; ++w)
+                if (w < d.n) {
+                  srow[d.col + w] = v[u][w];
+                  if (am >= 0 && v[u][w] > pb) {
+                    pb = v[u][w];
+                    pi = d.ch0 + w;
+                  }
+                }
+              if (am >= 0 && (am >> 30)) {
+                srow[am & 0xffff] = pb;
+                srow[(am & 0xffff) + 1] = __int_as_float(pi);
+                pb = -INFINITY;
+                pi = 0x7fffffff;
+              }
             }
-        }
-        float S[kBlk];
-#pragma unroll
-        for (int k = 0; k < kBlk; ++k) S[k] = (k < nb) ? seg_sum(v[k], use) : 0.f;
-        if (complete) {
-          for (int bb = 0; bb < src.n_layers; ++bb) {
-            const LayerDev& L = md.L[src.layers[bb]];
-            if (L.rule == MEM_RULE_CLASSMAX) continue;
-            RuleCoef r;
-#pragma unroll
-            for (int u = 0; u < kPre; ++u)
-              if (u == bb) r = co[u];
-            if (bb >= kPre) r = layer_coef(md, src.layers[bb], g, fl, N, rN);
-            apply_block(L, g * L.S + cb, S, nb, r);
           }
         }
-        if (partial) {
-          float* r = rec + src.acc_off + cb;
-#pragma unroll
-          for (int k = 0; k < kBlk; ++k)
-            if (k < nb) r[k] = S[k];
+      }
+      __syncthreads();
+      if (r0 == 0 && t < np) {
+        // outlier gate against the pre-call state: height sums of the point
+        const int r = s.pinf[t] >> 1;
+        const MapCall* mc = md.n_maps > 1 ? job->maps + s.key[t + 1] / md.W2 : &s.mc0;
+        float z, vm;
+        eval_zvm(md, *mc, xs, ys, zs, z, vm);
+        const bool rej = (s.fl[r] & kFlagValid) && gate_reject(z, s.h0[r], s.v0[r], vm, md.lam2);
+        const float w = __frcp_rn(vm);
+        float* row = s.stage + t * kQS;
+        row[0] = rej ? 0.f : w;
+        row[1] = rej ? 0.f : z * w;
+        row[2] = rej ? 0.f : 1.f;
+        row[3] = rej ? 1.f : 0.f;
+      }
+      // per-point arg-max of a source whose channels began in an earlier round
+      for (int c = 0; c < nr && s.fallback; ++c) {
+        if (s.col_ch[c] != kChArgV) continue;  // uniform
+        const SrcDev& src = s.src[s.col_src[c]];
+        if (t < np && slot_off(r0) > src.acc_off) {
+          float pb = -INFINITY;
+          int pi = 0x7fffffff;
+          for (int k = 0; k < src.C; ++k) {
+            const float v = ld_any(src.data, src.dtype, (int64_t)s.idx[t] * src.C + k);
+            if (v > pb) {
+              pb = v;
+              pi = k;
+            }
+          }
+          s.stage[t * kQS + c] = pb;
+          s.stage[t * kQS + c + 1] = __int_as_float(pi);
         }
       }
-      // class max of the run: one segmented scan of (value, class) pairs
-      float best = -INFINITY;
-      int bid = -1;
-      if (src.has_classmax) {
+      __syncthreads();
+      // walk: thread (segment, column) over the segment's points in order; an
+      // arg-max column carries (value, channel) pairs from its column and the next
+      {
+        const int nseg = max(1, min(min(kFT / nr, kSegMax), np));
+        const int len = (np + nseg - 1) / nseg;
+        const int sg = t / nr, c = t - sg * nr;
+        const int i0 = sg * len, i1 = min(i0 + len, np);
+        const bool on = sg < nseg && i0 < i1 && s.col_ch[c] != kChArgI;
+        const bool pair = on && s.col_ch[c] == kChArgV;
+        const bool cont0 = on && i0 > 0 && !((s.endbits[(i0 - 1) >> 5] >> ((i0 - 1) & 31)) & 1u);
+        if (on && !pair) {
+          // run ends of the segment as a bit mask; values eight at a time
+          const int n = i1 - i0;
+          const int wb = i0 >> 5, ob = i0 & 31;
+          u64 e64 = s.endbits[wb];
+          if (wb + 1 < kFT / 32) e64 |= (u64)s.endbits[wb + 1] << 32;
+          const u32 em = (u32)(e64 >> ob);
+          bool cont = cont0;
+          float a = 0.f;
+          int start = i0;  // first point of the open run in this segment
+          for (int j0 = 0; j0 < n; j0 += 8) {
+            float v[8];
 #pragma unroll
-        for (int s = 0; s < 5; ++s) {
-          const float ov = __shfl_up_sync(0xffffffffu, pbest, 1 << s);
-          const int oi = __shfl_up_sync(0xffffffffu, pbid, 1 << s);
-          if (use[s] && (ov > pbest || (ov == pbest && oi < pbid))) {
-            pbest = ov;
-            pbid = oi;
+            for (int u = 0; u < 8; ++u) v[u] = j0 + u < n ? s.stage[(i0 + j0 + u) * kQS + c] : 0.f;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              if (j0 + u < n) {
+                a += v[u];
+                if ((em >> (j0 + u)) & 1u) {
+                  if (cont) s.hp[sg * nr + c].x = a;
+                  else s.stage[start * kQS + c] = a;
+                  cont = false;
+                  a = 0.f;
+                  start = i0 + j0 + u + 1;
+                }
+              }
+            }
+          }
+          if (!((em >> (n - 1)) & 1u)) s.tp[sg * nr + c].x = a;
+        } else if (pair) {
+          bool cont = cont0;
+          float2 m = make_float2(-INFINITY, __int_as_float(0x7fffffff));
+          for (int i = i0; i < i1; ++i) {
+            m = cm_comb(m, make_float2(s.stage[i * kQS + c], s.stage[i * kQS + c + 1]));
+            const int pf = s.pinf[i];
+            if (pf & 1) {
+              if (cont) {
+                s.hp[sg * nr + c] = m;
+              } else {
+                float* row = s.stage + s.rstart[pf >> 1] * kQS + c;
+                row[0] = m.x;
+                row[1] = m.y;
+              }
+              cont = false;
+              m = make_float2(-INFINITY, __int_as_float(0x7fffffff));
+            }
+          }
+          if (!(s.pinf[i1 - 1] & 1)) s.tp[sg * nr + c] = m;
+        }
+        __syncthreads();
+        // runs that cross segments: finished by the segment holding their last point
+        if (cont0) {
+          const int r = s.pinf[i0] >> 1;
+          if (s.rstart[r + 1] <= i1) {
+            const int s0 = s.rstart[r] / len;
+            float* row = s.stage + s.rstart[r] * kQS + c;
+            if (!pair) {
+              float a = s.tp[s0 * nr + c].x;
+              for (int k = s0 + 1; k < sg; ++k) a += s.tp[k * nr + c].x;
+              row[0] = a + s.hp[sg * nr + c].x;
+            } else {
+              float2 a = s.tp[s0 * nr + c];
+              for (int k = s0 + 1; k < sg; ++k) a = cm_comb(a, s.tp[k * nr + c]);
+              a = cm_comb(a, s.hp[sg * nr + c]);
+              row[0] = a.x;
+              row[1] = a.y;
+            }
           }
         }
-        best = pbest;
-        bid = pbest == -INFINITY ? -1 : pbid;
-        if (partial) {
-          rec[src.acc_off + src.C] = best;
-          rec[src.acc_off + src.C + 1] = __int_as_float(bid);
+        __syncthreads();
+      }
+      // run sums of the round to the slots: tasks (run, column)
+      {
+        int r = t / nr, c = t - (t / nr) * nr;
+        const int dr = kFT / nr, dc = kFT - dr * nr;
+        for (int k = t; k < nruns * nr; k += kFT) {
+          fz_slot(md, acc, base + r)[slot_off(r0 + c)] = s.stage[s.rstart[r] * kQS + c];
+          r += dr;
+          c += dc;
+          if (c >= nr) {
+            c -= nr;
+            ++r;
+          }
         }
       }
-      if (complete) finish_source(md, src, g, fl, N, rN, best, bid);
+      r0 = re;
+      __syncthreads();  // the next round overwrites the stage
     }
-    if (complete) md.flags[g] = fl;
   }
 }
 
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-__device__ __forceinline__ u32 warp_sum_u(u32 v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
+// ---------------------------------------------------------------------------
+
+struct ApplySmem {
+  u32 base[kFT];  // per run: slot, cell, flags, first following tile (0: the run ends here)
+  u32 g[kFT];
+  u32 fl[kFT];
+  int cont[kFT];
+  float N[kFT], rN[kFT];  // observations of the cell in this call
+  LayerDev L[kMaxLayers];
+  SrcDev src[kMaxSources];
+  int tile;
+};
+
+// value at slot offset o, summed over the run's slot and its continuations
+// (in tile order)
+__device__ __forceinline__ float run_sum(const MapDev& md, int acc, u32 slot, int cont, int n_tiles, int o) {
+  float S = __ldcg(fz_slot(md, acc, slot) + o);
+  for (int tt = cont; tt > 0 && tt < n_tiles; ++tt) {
+    const float* sl = fz_slot(md, acc, fz_tile_base(md)[tt]);
+    S += __ldcg(sl + o);
+    if (__float_as_uint(__ldcg(sl + kSlotBits)) & kBitEnd) break;
+  }
+  return S;
 }
 
-// record of piece j (0 = the starting window w0) of a crossing cell
-__device__ __forceinline__ const float* span_rec(const float* part, int64_t w0, int64_t j, int acc) {
-  return part + ((w0 + j) * 2 + (j == 0 ? 1 : 0)) * (int64_t)acc;
+// One rule layer over tasks (run, channel) of the tile's runs, kApplyU tasks
+// per thread in flight (old values, prior variances and sums first).
+template <int RULE, int DT>
+__device__ __forceinline__ void apply_layer_t(const MapDev& md, const ApplySmem& s, const LayerDev& L, int l,
+                                              int o0, int nruns, int acc, int n_tiles) {
+  const int C = L.C, ntask = nruns * C;
+  int r = threadIdx.x / C, c = threadIdx.x - (threadIdx.x / C) * C;
+  const int dr = kFT / C, dc = kFT - dr * C;
+  for (int k0 = threadIdx.x; k0 < ntask; k0 += kApplyU * kFT) {
+    float old[kApplyU], s02[kApplyU], S[kApplyU];
+    int rr[kApplyU], cc[kApplyU];
+#pragma unroll
+    for (int u = 0; u < kApplyU; ++u) {
+      rr[u] = r;
+      cc[u] = c;
+      old[u] = s02[u] = S[u] = 0.f;
+      if (k0 + u * kFT < ntask) {
+        const u32 g = s.g[r];
+        if (s.fl[r] & (2u << l)) {
+          if (RULE != MEM_RULE_LATEST) old[u] = ld1t<DT>(L.data, (int64_t)g * L.S + c);
+          if (RULE == MEM_RULE_GAUSS) s02[u] = L.gvar[g];
+        }
+        S[u] = run_sum(md, acc, s.base[r], s.cont[r], n_tiles, o0 + c);
+      }
+      r += dr;
+      c += dc;
+      if (c >= C) {
+        c -= C;
+        ++r;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kApplyU; ++u) {
+      if (k0 + u * kFT < ntask) {
+        const int q = rr[u];
+        const bool obs = s.fl[q] & (2u << l);
+        const RuleCoef co = rule_coef(L, s.N[q], s.rN[q], obs, s02[u]);
+        st1t<DT>(L.data, (int64_t)s.g[q] * L.S + cc[u], rule_value_t<RULE>(L, old[u], S[u], co));
+      }
+    }
+  }
 }
 
-__global__ void __launch_bounds__(256) k_fuse_span(MapDev md, const PointJob* __restrict__ job) {
+__device__ __forceinline__ void apply_layer(const MapDev& md, const ApplySmem& s, const LayerDev& L, int l, int o0,
+                                            int nruns, int acc, int n_tiles) {
+#define MEM_AL(R, D) \
+  case R * 4 + D: apply_layer_t<R, D>(md, s, L, l, o0, nruns, acc, n_tiles); break;
+  switch (L.rule * 4 + L.dtype) {
+    MEM_AL(MEM_RULE_LATEST, MEM_F32) MEM_AL(MEM_RULE_LATEST, MEM_BF16) MEM_AL(MEM_RULE_LATEST, MEM_F16)
+    MEM_AL(MEM_RULE_EXPAVG, MEM_F32) MEM_AL(MEM_RULE_EXPAVG, MEM_BF16) MEM_AL(MEM_RULE_EXPAVG, MEM_F16)
+    MEM_AL(MEM_RULE_GAUSS, MEM_F32) MEM_AL(MEM_RULE_GAUSS, MEM_BF16) MEM_AL(MEM_RULE_GAUSS, MEM_F16)
+    MEM_AL(MEM_RULE_DIRICHLET, MEM_F32)
+    default: break;
+  }
+#undef MEM_AL
+}
+
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+__global__ void __launch_bounds__(kFT) k_fuse_apply(MapDev md, const PointJob* __restrict__ job) {
+  __shared__ ApplySmem s;
   const int64_t n_kept = *(volatile u32*)&md.counters[6];
-  const int64_t n_win = (n_kept + 31) >> 5;
+  const int n_tiles = (int)((n_kept + kFT - 1) / kFT);
   const int n_src = job->n_src;
   const int acc = job->acc;
-  const float* __restrict__ part = md.partial;
-  const int lane = threadIdx.x & 31;
-  const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w0 < n_win; w0 += wstride) {
-    const float* r0 = part + (w0 * 2 + 1) * (int64_t)acc;
-    if (__float_as_uint(r0[4]) != kRecStart) continue;  // warp-uniform
-    // number of pieces: walk the slot-0 flags of the following windows, 32 at a time
-    int64_t np = 0;
-    for (int64_t j0 = 1;; j0 += 32) {
-      const int64_t j = j0 + lane;
-      const u32 f = (w0 + j < n_win) ? __float_as_uint(span_rec(part, w0, j, acc)[4]) : kRecLast;
-      const u32 last = __ballot_sync(0xffffffffu, f == kRecLast);
-      if (last) {
-        np = j0 + (__ffs(last) - 1) + 1;
-        break;
+  const int t = threadIdx.x;
+  if (t < md.n_layers) s.L[t] = md.L[t];
+  if (t < n_src) s.src[t] = job->src[t];
+  __syncthreads();
+  bool any_gauss = false;  // Gaussian variances are written after every rule read them
+  for (int q = 0; q < n_src; ++q)
+    for (int b = 0; b < s.src[q].n_layers; ++b) any_gauss |= s.L[s.src[q].layers[b]].rule == MEM_RULE_GAUSS;
+  for (;;) {
+    __syncthreads();  // the previous tile is done with the shared arrays
+    if (t == 0) s.tile = atomicAdd(&md.counters[9], 1);
+    __syncthreads();
+    const int tile = s.tile;
+    if (tile >= n_tiles) break;
+    const u32 tb = fz_tile_base(md)[tile];
+    const int tr = (int)fz_tile_runs(md)[tile];
+    // runs that begin in this tile: all but a first run carried in
+    const int r_lo = (__float_as_uint(__ldcg(fz_slot(md, acc, tb) + kSlotBits)) & kBitHead) ? 0 : 1;
+    const int nruns = tr - r_lo;
+    // per run: totals over the run's slots, height update, class max, flags;
+    // the rule layers' rows are prefetched into L2 for the passes below
+    if (t < nruns) {
+      const u32 slot = tb + r_lo + t;
+      const float* hdr = fz_slot(md, acc, slot);
+      float sw = __ldcg(hdr), swz = __ldcg(hdr + 1);
+      u32 na = (u32)__ldcg(hdr + 2), nr = (u32)__ldcg(hdr + 3);
+      u32 n = __float_as_uint(__ldcg(hdr + kSlotN));
+      const u32 g = __float_as_uint(__ldcg(hdr + kSlotKey));
+      const u32 fl0 = __float_as_uint(__ldcg(hdr + kSlotFl));
+      for (int q = 0; q < n_src; ++q) {
+        const SrcDev& src = s.src[q];
+        for (int b = 0; b < src.n_layers; ++b) {
+          const int l = src.layers[b];
+          const LayerDev& L = s.L[l];
+          if (L.rule == MEM_RULE_CLASSMAX || L.rule == MEM_RULE_LATEST || !(fl0 & (2u << l))) continue;
+          const char* row = (const char*)L.data + (int64_t)g * L.S * (L.dtype == MEM_F32 ? 4 : 2);
+          const int bytes = L.S * (L.dtype == MEM_F32 ? 4 : 2);
+          for (int o = 0; o < bytes; o += 128) prefetch_l2(row + o);
+          prefetch_l2(row + bytes - 1);
+        }
       }
+      int cont = 0;
+      if (!(__float_as_uint(__ldcg(hdr + kSlotBits)) & kBitEnd)) {
+        // the run continues: add the following tiles' first pieces
+        cont = tile + 1;
+        for (int tt = tile + 1; tt < n_tiles; ++tt) {
+          const float* sl = fz_slot(md, acc, fz_tile_base(md)[tt]);
+          sw += __ldcg(sl);
+          swz += __ldcg(sl + 1);
+          na += (u32)__ldcg(sl + 2);
+          nr += (u32)__ldcg(sl + 3);
+          n += __float_as_uint(__ldcg(sl + kSlotN));
+          if (__float_as_uint(__ldcg(sl + kSlotBits)) & kBitEnd) break;
+        }
+      }
+      const float N = (float)n, rN = __frcp_rn((float)n);
+      s.base[t] = slot;
+      s.g[t] = g;
+      s.fl[t] = fl0;
+      s.cont[t] = cont;
+      s.N[t] = N;
+      s.rN[t] = rN;
+      // Kalman height update in information form (float32) + cumulative counts
+      u32 fl = fl0;
+      const float h0 = __ldcg(hdr + kSlotH0), v0 = __ldcg(hdr + kSlotV0);
+      float h = h0, v = v0;
+      if (na > 0) {
+        if (fl & kFlagValid) {
+          const float P = __frcp_rn(v0) + sw;
+          h = (h0 * __frcp_rn(v0) + swz) * __frcp_rn(P);
+          v = __frcp_rn(P);
+        } else {
+          h = swz * __frcp_rn(sw);
+          v = __frcp_rn(sw);
+          fl |= kFlagValid;
+        }
+      }
+      if (nr > 0 && md.outlier_var != 0.f) v = fmaf(md.outlier_var, (float)nr, v);
+      md.h[g] = h;
+      md.var[g] = v;
+      md.n_acc[g] = __float_as_uint(__ldcg(hdr + kSlotNacc)) + na;
+      md.n_rej[g] = __float_as_uint(__ldcg(hdr + kSlotNrej)) + nr;
+      // class max; then every bound layer is observed
+      for (int q = 0; q < n_src; ++q) {
+        const SrcDev& src = s.src[q];
+        if (src.has_classmax) {
+          const int o = src.acc_off + src.C;
+          float2 bv = make_float2(__ldcg(hdr + o), __ldcg(hdr + o + 1));
+          for (int tt = cont; tt > 0 && tt < n_tiles; ++tt) {
+            const float* sl = fz_slot(md, acc, fz_tile_base(md)[tt]);
+            bv = cm_comb(bv, make_float2(__ldcg(sl + o), __ldcg(sl + o + 1)));
+            if (__float_as_uint(__ldcg(sl + kSlotBits)) & kBitEnd) break;
+          }
+          const int bid = bv.x == -INFINITY ? -1 : __float_as_int(bv.y);
+          for (int b = 0; b < src.n_layers; ++b) {
+            const LayerDev& L = s.L[src.layers[b]];
+            if (L.rule == MEM_RULE_CLASSMAX) {
+              float* d = (float*)L.data + (int64_t)g * 2;
+              d[0] = (float)bid;
+              d[1] = bv.x;
+            }
+          }
+        }
+        for (int b = 0; b < src.n_layers; ++b) fl |= 2u << src.layers[b];
+      }
+      md.flags[g] = fl;
     }
-    const u32 key = __float_as_uint(r0[5]);
-    const int64_t g = key;
-    u32 fl = md.flags[g];
-    const float h0 = md.h[g], v0 = md.var[g];
-    // height: lanes over pieces, then a fixed-order tree
-    HeightAcc a = {0.f, 0.f, 0u, 0u};
-    for (int64_t j = lane; j < np; j += 32) {
-      const float* r = span_rec(part, w0, j, acc);
-      a.sw += r[0];
-      a.swz += r[1];
-      a.na += __float_as_uint(r[2]);
-      a.nr += __float_as_uint(r[3]);
-    }
-    a.sw = warp_sum(a.sw);
-    a.swz = warp_sum(a.swz);
-    a.na = warp_sum_u(a.na);
-    a.nr = warp_sum_u(a.nr);
-    const float N = (float)(a.na + a.nr), rN = __frcp_rn(N);
-    if (lane == 0) height_update(md, g, fl, h0, v0, a);
-    fl = __shfl_sync(0xffffffffu, fl, 0);
+    __syncthreads();
+    // rules, layer by layer (they read the pre-call observed bits kept in shared memory)
     for (int q = 0; q < n_src; ++q) {
-      const SrcDev& src = job->src[q];
-      float best = -INFINITY;
-      int bid = -1;
-      for (int cb = 0; cb < src.C; cb += 32) {
-        const int c = cb + lane;
-        const bool on = c < src.C;
-        float s = 0.f;
-        if (on) {
-          int64_t j = 0;
-          for (; j + 8 <= np; j += 8) {
-            float x[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) x[u] = (span_rec(part, w0, j + u, acc) + src.acc_off)[c];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) s += x[u];
-          }
-          for (; j < np; ++j) s += (span_rec(part, w0, j, acc) + src.acc_off)[c];
-          for (int bb = 0; bb < src.n_layers; ++bb) {
-            const LayerDev& L = md.L[src.layers[bb]];
-            if (L.rule != MEM_RULE_CLASSMAX)
-              apply_rule(L, g * L.S + c, s, layer_coef(md, src.layers[bb], g, fl, N, rN));
-          }
-        }
+      const SrcDev& src = s.src[q];
+      for (int b = 0; b < src.n_layers; ++b) {
+        const int l = src.layers[b];
+        if (s.L[l].rule != MEM_RULE_CLASSMAX) apply_layer(md, s, s.L[l], l, src.acc_off, nruns, acc, n_tiles);
       }
-      if (src.has_classmax) {
-        // (value, class) of every piece: largest value, smallest class on ties
-        float bv = -INFINITY;
-        int bi = 0x7fffffff;
-        for (int64_t j = lane; j < np; j += 32) {
-          const float* r = span_rec(part, w0, j, acc) + src.acc_off + src.C;
-          const float ov = r[0];
-          const int oi = __float_as_int(r[1]);
-          if (ov > bv || (ov == bv && oi < bi)) {
-            bv = ov;
-            bi = oi;
-          }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
-          const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-          if (ov > bv || (ov == bv && oi < bi)) {
-            bv = ov;
-            bi = oi;
-          }
-        }
-        best = bv;
-        bid = bv == -INFINITY ? -1 : bi;
-      }
-      if (lane == 0) finish_source(md, src, g, fl, N, rN, best, bid);
-      fl = __shfl_sync(0xffffffffu, fl, 0);
     }
-    if (lane == 0) md.flags[g] = fl;
+    if (any_gauss) {
+      __syncthreads();  // every rule read its Gaussian prior variance
+      if (t < nruns) {
+        const u32 g = s.g[t];
+        const u32 fl = s.fl[t];
+        for (int q = 0; q < n_src; ++q)
+          for (int b = 0; b < s.src[q].n_layers; ++b) {
+            const int l = s.src[q].layers[b];
+            const LayerDev& L = s.L[l];
+            if (L.rule != MEM_RULE_GAUSS) continue;
+            const bool obs = fl & (2u << l);
+            L.gvar[g] = rule_coef(L, s.N[t], s.rN[t], obs, obs ? L.gvar[g] : 0.f).var_new;
+          }
+      }
+    }
+    if (t == 0) {
+      if (nruns) atomicAdd(&md.counters[5], (u32)nruns);
+      u32 crossing = 0;
+      for (int r = 0; r < nruns; ++r) crossing += s.cont[r] != 0;
+      if (crossing) atomicAdd(&md.counters[4], crossing);
+    }
   }
 }
 
@@ -854,10 +1056,13 @@ __global__ void k_time_update(MapDev md, int64_t cells) {
 namespace memh {
 using namespace memk;
 
+// resident CTAs per SM of the fuse kernels (their persistent grids)
+static int g_sums_ctas_per_sm = 1, g_apply_ctas_per_sm = 1;
+
 template <int RB>
 static size_t sort_smem() {
   constexpr int RADIX = 1 << RB;
-  return sizeof(u32) * ((kSortThreads / 32) * RADIX + 2 * kTile + 3 * RADIX);
+  return sizeof(u32) * ((kSortThreads / 32) * RADIX + 2 * kTile + 4 * RADIX);
 }
 
 template <int RB>
@@ -886,20 +1091,16 @@ static cudaError_t launch_rb(Map* m, const PointJob* d_job, cudaStream_t st) {
     k_points_key<RB><<<sms * bps, 256, sizeof(u32) * (P * (1 << RB) + 1), st>>>(md, d_job, P);
   }
   {
-    ProfScope ps(m, kProfDigits, st);
-    k_digit_scan<<<1, 1024, 0, st>>>(md, P, 1 << RB);
-  }
-  {
     ProfScope ps(m, kProfSort, st);
     for (int p = 0; p < P; ++p) k_onesweep<RB><<<sms * 2, kSortThreads, sort_smem<RB>(), st>>>(md, d_job, p);
   }
   {
-    ProfScope ps(m, kProfFuseWindow, st);
-    k_fuse_window<<<sms * bps, 256, 0, st>>>(md, d_job, P & 1);
+    ProfScope ps(m, kProfFuseSums, st);
+    k_fuse_sums<<<sms * g_sums_ctas_per_sm, kFT, sizeof(SumSmem), st>>>(md, d_job, P & 1);
   }
   {
-    ProfScope ps(m, kProfFuseSpan, st);
-    k_fuse_span<<<sms * bps, 256, 0, st>>>(md, d_job);
+    ProfScope ps(m, kProfFuseApply, st);
+    k_fuse_apply<<<sms * g_apply_ctas_per_sm, kFT, 0, st>>>(md, d_job);
   }
   if (md.time_var != 0.f) {
     ProfScope ps(m, kProfTime, st);
@@ -910,7 +1111,15 @@ static cudaError_t launch_rb(Map* m, const PointJob* d_job, cudaStream_t st) {
 }
 
 cudaError_t prepare_kernels() {
-  cudaError_t e = set_attrs<8>();
+  cudaError_t e = cudaFuncSetAttribute(k_fuse_sums, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sizeof(SumSmem));
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_sums_ctas_per_sm, k_fuse_sums, kFT, sizeof(SumSmem));
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_apply_ctas_per_sm, k_fuse_apply, kFT, 0);
+  if (g_sums_ctas_per_sm < 1) g_sums_ctas_per_sm = 1;
+  if (g_apply_ctas_per_sm < 1) g_apply_ctas_per_sm = 1;
+  if (e == cudaSuccess) e = set_attrs<8>();
   if (e == cudaSuccess) e = set_attrs<9>();
   if (e == cudaSuccess) e = set_attrs<10>();
   return e;

@@ -171,3 +171,63 @@ def test_bf16_and_f16_feature_storage(torch):
         o.fuse_points(cl.xyz, cl.T, [((cl.feat,), [0, 1, 2]), (cl.rgb, [3])])
         g.fuse_pointcloud(cuda_xyz(cl), cl.T, [(feat_t, [0, 1, 2]), (torch.from_numpy(cl.rgb).cuda(), [3])])
         compare_states(gpu_state(g), o, what=f"bf16 scan {k}", bf16_rel=2.0 ** -7)
+
+
+def test_graph_replay_on_a_side_stream_equals_eager(torch):
+    """On a stream of its own the point path is captured once and replayed from a CUDA graph;
+    the layers must be bit-identical to eager launches on the default stream, pose after pose."""
+    from paper_2309_16818_gb300 import mem as M
+    c = synth.config2(n_poses=3, scale=0.25)
+    layers = [M.Layer(3, M.LATEST), M.Layer(20, M.DIRICHLET), M.Layer(20, M.CLASSMAX),
+              M.Layer(20, M.EXPAVG, w=0.1)]
+    eager = M.Map(c["W"], c["res"], layers, max_points=1 << 16)
+    replay = M.Map(c["W"], c["res"], layers, max_points=1 << 16)
+    side = torch.cuda.Stream()
+    for k, scan in enumerate(c["scans"]):
+        srcs = [(torch.from_numpy(scan.rgb).cuda(), [0]), (torch.from_numpy(scan.probs).cuda(), [1, 2, 3])]
+        xyz = cuda_xyz(scan)
+        eager.move(c["poses"][k][:2])
+        eager.fuse_pointcloud(xyz, scan.T, srcs)
+        torch.cuda.synchronize()
+        with torch.cuda.stream(side):
+            replay.move(c["poses"][k][:2])
+            replay.fuse_pointcloud(xyz, scan.T, srcs)
+        side.synchronize()
+        eager.check()
+        replay.check()
+        for layer in (M.LAYER_HEIGHT, M.LAYER_VARIANCE, M.LAYER_VALID, M.LAYER_NACC, M.LAYER_NREJ, 0, 1, 2, 3):
+            a = eager.get_layer(layer).cpu().numpy()
+            b = replay.get_layer(layer).cpu().numpy()
+            assert np.array_equal(a.view(np.uint8), b.view(np.uint8)), (k, layer)
+
+
+def test_run_to_run_identical_with_moves(torch):
+    """Every sum is taken in a fixed order, so the same pose sequence (with map moves, which
+    wrap the ring-buffer keys) on fresh maps must give bit-identical layers, repeatedly."""
+    from paper_2309_16818_gb300 import mem as M
+    c = synth.config2(n_poses=4, scale=1.0)
+    layers = [M.Layer(3, M.LATEST), M.Layer(20, M.DIRICHLET), M.Layer(20, M.CLASSMAX),
+              M.Layer(20, M.EXPAVG, w=0.1)]
+    data = [(cuda_xyz(s), torch.from_numpy(s.rgb).cuda(), torch.from_numpy(s.probs).cuda()) for s in c["scans"]]
+    ref = None
+    for trial in range(4):
+        g = M.Map(c["W"], c["res"], layers, max_points=1 << 20)
+        if trial % 2:
+            g.set_tuning(9, 8)
+        out = []
+        for k, s in enumerate(c["scans"]):
+            g.move(c["poses"][k][:2])
+            x, r, p = data[k]
+            g.fuse_pointcloud(x, s.T, [(r, [0]), (p, [1, 2, 3])])
+            g.check()
+            valid = g.get_layer(M.LAYER_VALID).cpu().numpy().astype(bool)
+            for lay in (M.LAYER_HEIGHT, M.LAYER_VARIANCE, M.LAYER_NACC, M.LAYER_NREJ):
+                out.append(np.where(valid, g.get_layer(lay).cpu().numpy(), 0).tobytes())
+            out.append(valid.tobytes())
+            for lay in (0, 1, 2, 3):
+                out.append(g.get_layer(lay).cpu().numpy().tobytes())
+        if ref is None:
+            ref = out
+        else:
+            for j, (a, b) in enumerate(zip(ref, out)):
+                assert a == b, (trial, j)
