@@ -265,30 +265,25 @@ def run_ours(args):
     P = stats[0]["passes"]
     payload = 3 + 80
     cb = cell_bytes(layers, M)
-    hdr = 16  # words of a fuse slot header
-    slot_words = hdr + 3 + 20 + 2
     algo = {  # algorithmic bytes per launch
         "key": n_mean * 16,
         "radix_sort": n_mean * 16,
-        # keys + indices, coordinates and payload of every kept point, the pre-call
-        # state of every touched cell, the slots it writes
-        "fuse_sums": kept * (4 + 4 + 12 + payload) + cells * (20 + 4 * slot_words),
-        # slots read, then every layer of every touched cell read and written
-        "fuse_apply": cells * (4 * slot_words + cb),
+        # keys + indices, coordinates and payload of every kept point, then every
+        # layer of every touched cell read and written
+        "fuse_tiles": kept * (4 + 4 + 12 + payload) + cells * cb,
     }
-    launches = {"key": K, "radix_sort": K * P, "fuse_sums": K, "fuse_apply": K, "move": prof["move"][1]}
+    launches = {"key": K, "radix_sort": K * P, "fuse_tiles": K, "fuse_cross": K, "move": prof["move"][1]}
     kern = {}
     for name, (ms, calls) in prof.items():
         if calls:
             kern[name] = {"ms_total": round(ms, 4), "launches": launches.get(name, calls),
                           "us_per_launch": round(1e3 * ms / launches.get(name, calls), 3)}
-    cand = {k: prof[k][0] for k in ("key", "radix_sort", "fuse_sums", "fuse_apply")}
+    cand = {k: prof[k][0] for k in ("key", "radix_sort", "fuse_tiles")}
     dom = max(cand, key=cand.get)
     per_launch_s = cand[dom] / 1e3 / launches.get(dom, K)
     peak, peak_kind = peaks()
     achieved = algo[dom] / per_launch_s / 1e9
-    ncu_name = {"fuse_sums": "k_fuse_sums", "fuse_apply": "k_fuse_apply", "radix_sort": "k_onesweep",
-                "key": "k_points_key"}[dom]
+    ncu_name = {"fuse_tiles": "k_fuse_tiles", "radix_sort": "k_onesweep", "key": "k_points_key"}[dom]
     traffic = ncu_traffic(ncu_name)
     roofline = {"bound": "hbm", "kernel": ncu_name, "achieved": round(achieved, 1), "peak": peak,
                 "peak_kind": f"{peak_kind} (copy bandwidth)", "unit": "GB/s",
@@ -298,7 +293,7 @@ def run_ours(args):
     step_bytes = n_mean * 12 + kept * payload + cells * cb
     step_frac = step_bytes / (dev_s / K) / 1e9 / peak
 
-    gpu_launches = int(sum(launches[k] for k in ("key", "radix_sort", "fuse_sums", "fuse_apply"))
+    gpu_launches = int(sum(launches[k] for k in ("key", "radix_sort", "fuse_tiles", "fuse_cross"))
                        + prof["move"][1])
 
     # ---- end to end through the public API with host buffers

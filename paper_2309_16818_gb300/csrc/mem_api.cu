@@ -575,6 +575,74 @@ static mem_status check_sources(const Map* m, int32_t n_sources, const mem_sourc
   return MEM_OK;
 }
 
+void memh::build_fuse_tables(PointJob& job, int acc_raw, const mem_map_config& cfg) {
+  memk::FuseTables& f = job.ft;
+  memset(&f, 0, sizeof(f));
+  const int n_src = job.n_src;
+  for (int q = 0; q < n_src; ++q) {
+    int nl = 0;
+    for (int b = 0; b < job.src[q].n_layers; ++b) {
+      const int l = job.src[q].layers[b];
+      const int rule = cfg.layers[l].rule;
+      if (rule != MEM_RULE_CLASSMAX) f.rlay[q][nl++] = l;
+      if (rule == MEM_RULE_GAUSS) f.any_gauss = 1;
+    }
+    f.nrlay[q] = nl;
+  }
+  const int G = acc_raw - (kSlotHdr - 4);
+  f.ncol = G;
+  f.one_round = G <= memk::kFuseQ;
+  if (!f.one_round) return;
+  // columns: height sums, then each source's channels and arg-max pair
+  for (int c = 0; c < G; ++c) {
+    f.col_src[c] = -1;
+    f.col_ch[c] = c;
+    if (c < 4) continue;
+    const int o = c + (kSlotHdr - 4);
+    int q = 0;
+    for (int k = 1; k < n_src; ++k)
+      if (job.src[k].acc_off <= o) q = k;
+    const int ch = o - job.src[q].acc_off;
+    f.col_src[c] = q;
+    f.col_ch[c] = ch < job.src[q].C ? ch : (ch == job.src[q].C ? -1 : -2);
+  }
+  // staging chunks: runs of up to four consecutive channels of one source,
+  // aligned to four channels
+  int n = 0;
+  for (int c = 0; c < G; ++c) {
+    const int q = f.col_src[c], ch = f.col_ch[c];
+    if (q < 0 || ch < 0) continue;
+    const bool extend = n > 0 && f.ck[n - 1].n < 4 && (ch & 3) != 0 && f.col_src[c - 1] == q &&
+                        f.col_ch[c - 1] == ch - 1 && f.ck[n - 1].col + f.ck[n - 1].n == c;
+    if (extend) {
+      ++f.ck[n - 1].n;
+      continue;
+    }
+    memk::ChunkDesc& d = f.ck[n++];
+    d.data = job.src[q].data;
+    d.C = job.src[q].C;
+    d.ch0 = ch;
+    d.col = c;
+    d.n = 1;
+    d.dtype = job.src[q].dtype;
+    d.vec = job.src[q].vec_ok;
+    d.src = q;
+  }
+  f.n_ck = n;
+  for (int k = 0; k < n; ++k) {
+    const int q = f.ck[k].src;
+    const int av = f.ck[k].col - f.ck[k].ch0 + job.src[q].C;  // arg-max value column
+    const bool last = k + 1 == n || f.ck[k + 1].src != q;
+    f.ck[k].am = job.src[q].has_classmax ? (av | (last ? (1 << 30) : 0)) : -1;
+  }
+  for (int q = 0; q < n_src; ++q) {
+    f.qc0[q] = job.src[q].acc_off - (kSlotHdr - 4);
+    f.qch0[q] = 0;
+    f.qn[q] = job.src[q].C;
+    if (job.src[q].has_classmax) f.pair_col[f.n_pair++] = f.qc0[q] + job.src[q].C;
+  }
+}
+
 static mem_status ensure_capacity(Map* m, int64_t n) {
   if (n <= m->md.cap) return MEM_OK;
   cudaError_t e = cudaDeviceSynchronize();
@@ -606,11 +674,14 @@ static mem_status run_points(Map* m, int nm, const int64_t* offsets, int64_t n, 
     job->src[q].acc_off = acc;
     acc += src[q].C + 2 * src[q].has_classmax;  // channel sums, then (max value, class)
   }
+  build_fuse_tables(*job, acc, m->cfg);
+  acc = (acc + 3) / 4 * 4;  // slots start on 16-byte boundaries (vector loads of their headers)
   job->acc = acc;
   {
     cudaError_t e = ensure_partial(m, acc);
     if (e != cudaSuccess) return cuda_fail(e, "partial-record buffer");
   }
+  if (((uintptr_t)m->md.partial & 15) != 0) return fail(MEM_ERR_STATE, "fuse scratch not 16-byte aligned");
   job->maps = (const MapCall*)(m->d_job + sizeof(PointJob));
   job->offsets = nm > 1 ? (const int64_t*)(m->d_job + sizeof(PointJob) + sizeof(MapCall) * nm) : nullptr;
   for (int b = 0; b < nm; ++b) {

@@ -51,7 +51,7 @@ struct Map {
 };
 
 // profile slots
-enum { kProfKey = 0, kProfDigits, kProfSort, kProfUnused3, kProfFuseSums, kProfFuseApply,
+enum { kProfKey = 0, kProfDigits, kProfSort, kProfUnused3, kProfFuseTiles, kProfFuseCross,
        kProfTime, kProfImage, kProfMove, kProfSlots };
 
 // Brackets a launch group with events when profiling is on.
@@ -80,6 +80,9 @@ cudaError_t alloc_scratch(Map* m, int64_t cap);
 void free_scratch(Map* m);
 int key_bits_for(const Map* m);
 cudaError_t prepare_kernels();
+// stage layout and rule-layer lists of a point-path call (job.src, n_src and
+// the raw slot length `acc_raw` set), as the fuse kernel reads them
+void build_fuse_tables(memk::PointJob& job, int acc_raw, const mem_map_config& cfg);
 mem_status api_fail(mem_status s, const char* fmt, ...);
 mem_status api_cuda_fail(cudaError_t e, const char* what);
 

@@ -21,14 +21,15 @@ constexpr int kDevErrTimeout = 1;
 constexpr int kFuseTile = 128;               // sorted points per tile of the fuse kernels
 constexpr int kSlotHdr = 16;                 // words of a fuse slot before its channel sums
 // fuse slot header: sum w, sum w z, accepted, rejected (floats), then (bits)
-// cell key, points, begin/end bits, pre-call flags, height, variance,
-// accepted and rejected counts
+// cell key, points in the piece, used/begin/end bits, pre-call flags,
+// height, variance, accepted and rejected counts
 enum { kSlotKey = 4, kSlotN, kSlotBits, kSlotFl, kSlotH0, kSlotV0, kSlotNacc, kSlotNrej };
+static_assert(kSlotHdr % 4 == 0 && kSlotKey % 4 == 0 && kSlotH0 % 4 == 0, "16-byte aligned header groups");
 
-// words of the fuse scratch for `cap` points: tile tables, then at most one
-// slot per point (every run piece of a tile holds at least one point)
+// words of the fuse scratch for `cap` points: two slots of `acc` words per
+// tile (`acc` a multiple of 4, so every slot is 16-byte aligned)
 __host__ __device__ constexpr int64_t fuse_scratch_words(int64_t cap, int acc) {
-  return 2 * (cap / kFuseTile + 2) + cap * (int64_t)acc;
+  return 2 * (cap / kFuseTile + 2) * (int64_t)acc;
 }
 // Per-layer static description (device copy of mem_layer_desc + derived).
 struct LayerDev {
@@ -86,6 +87,36 @@ struct SrcDev {
   int acc_off;       // offset of this source's sums (then maxima) in a partial record
 };
 
+constexpr int kFuseQ = 32;  // stage columns of the fuse kernel per round
+
+// Up to four consecutive channels of one source that the fuse kernel stages
+// together.
+struct __align__(16) ChunkDesc {
+  const void* data;
+  int C, ch0;       // row length, first channel
+  int col, n;       // first stage column, channels
+  int dtype, vec;   // storage, 16-byte aligned rows
+  int am;           // arg-max value column of the source (-1: none); bit 30: last chunk
+  int src;
+  int unused[2];
+};
+
+// Stage layout of the fuse kernel, built on the host for a call whose
+// columns fit one round (one_round != 0); otherwise the kernel builds the
+// column part round by round. The rule-layer lists hold for every call.
+struct FuseTables {
+  int ncol;  // columns of the call: 4 height sums, then per source C channels (+ arg-max pair)
+  int one_round, n_ck, n_pair;
+  int col_src[kFuseQ];  // per column: source (-1: height sums)
+  int col_ch[kFuseQ];   // channel, -1 / -2 for a source's arg-max value / channel, or height sum
+  ChunkDesc ck[kFuseQ];
+  int pair_col[kMaxSources];  // arg-max value columns
+  int qc0[kMaxSources], qch0[kMaxSources], qn[kMaxSources];  // per source: first column, channel, count
+  int rlay[kMaxSources][kMaxSrcLayers];  // per source: its layers other than class max
+  int nrlay[kMaxSources];
+  int any_gauss;
+};
+
 // Per-call job of the point path, resident in device memory so the whole
 // kernel sequence can be replayed from a CUDA graph.
 struct PointJob {
@@ -97,6 +128,7 @@ struct PointJob {
   int n_src;
   int acc;  // words per fuse slot: kSlotHdr, then per source C sums (+ max value, class)
   SrcDev src[kMaxSources];
+  FuseTables ft;
 };
 
 // ---------------------------------------------------------------------------

@@ -6,11 +6,12 @@
 //   k_onesweep      stable LSD radix-sort pass with decoupled look-back,
 //                   one per digit (keys = map * W*W + physical cell); each
 //                   CTA first scans the digit counts into global offsets
-//   k_fuse_sums     per tile of sorted points: outlier gate, then the sums of
-//                   every cell's quantities (a reduce-by-key in a fixed order)
-//   k_fuse_apply    per cell: Kalman height update, then every multi-modal
-//                   layer's rule (no float atomics, fixed summation order, so
-//                   the results are run-to-run identical)
+//   k_fuse_tiles    per tile of sorted points: outlier gate, sums of every
+//                   cell's quantities (a reduce-by-key in a fixed order), then
+//                   for the cells inside the tile the Kalman height update and
+//                   every multi-modal layer's rule
+//   k_fuse_cross    the same for the cells whose points cross tiles (no float
+//                   atomics, fixed summation order: run-to-run identical)
 //
 // Every kernel reads its per-call parameters from the device-resident job, so
 // the sequence replays unchanged from a CUDA graph.
@@ -328,7 +329,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(MapDev md, const Poin
 // The sorted points are cut into tiles of kFuseTile; the points of one cell
 // form one run of the sorted order, and a run may cross tile boundaries.
 //
-// k_fuse_sums: one CTA per tile (persistent, tiles taken from a counter).
+// k_fuse_tiles: one CTA per tile (persistent, tiles taken from a counter).
 //   Every quantity summed per cell is a column of a stage in shared memory
 //   with one row per point: the four height sums (after the outlier gate
 //   against the pre-call state), then every source's channels, then, for a
@@ -336,13 +337,13 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(MapDev md, const Poin
 //   its channel. Up to kQ columns are staged at once (a round); a thread
 //   walks one column over a fixed segment of the tile's points in point
 //   order, and the pieces of a run that crosses segments are added in
-//   segment order. Each run piece of the tile leaves one slot: its sums,
-//   its cell, its pre-call state, and whether the run begins / ends in the
-//   tile.
-// k_fuse_apply: one CTA per tile again. The tile completes every run that
-//   begins in it: a run that continues past the tile adds the slots of the
-//   following tiles' first runs, in tile order. Then the Kalman height update
-//   and every layer's rule, then class max, Gaussian variances and flags.
+//   segment order. A run whose points all lie in the tile is then fused
+//   right there (Kalman height update, every layer's rule, class max,
+//   flags); the layers' rows of the tile's cells were prefetched into L2 when
+//   the tile started. A run that crosses the tile's first or last boundary
+//   leaves its piece's sums in one of the tile's two slots.
+// k_fuse_cross: one warp per run that crosses tile boundaries (the tile
+//   where it begins): adds its pieces in tile order, then fuses it.
 // The float32 summation order depends only on the sorted order, which is
 // deterministic: results are identical from run to run.
 
@@ -354,16 +355,14 @@ constexpr int kStageU = 6;      // staging chunks in flight per thread
 constexpr int kApplyU = 4;      // rule tasks in flight per thread
 constexpr u32 kBitHead = 1u;    // slot bits: the run begins in the tile
 constexpr u32 kBitEnd = 2u;     //            the run ends in the tile
+constexpr u32 kBitUsed = 4u;    //            the slot holds a piece of this call
 constexpr int kChArgV = -1;     // column of a source's arg-max value
 constexpr int kChArgI = -2;     // column of a source's arg-max channel
 
-// fuse scratch: [tile_base | tile_runs | slots]
-__device__ __forceinline__ u32* fz_tile_base(const MapDev& md) { return (u32*)md.partial; }
-__device__ __forceinline__ u32* fz_tile_runs(const MapDev& md) {
-  return (u32*)md.partial + (md.cap / kFT + 2);
-}
-__device__ __forceinline__ float* fz_slot(const MapDev& md, int acc, int64_t slot) {
-  return md.partial + 2 * (md.cap / kFT + 2) + slot * acc;
+// fuse scratch: two slots per tile, [0] the piece of a run carried in that
+// ends in the tile, [1] the piece of a run that continues past the tile
+__device__ __forceinline__ float* fz_slot(const MapDev& md, int acc, int tile, int k) {
+  return md.partial + (int64_t)(2 * tile + k) * acc;  // 16-byte aligned (acc % 4 == 0)
 }
 
 // slot offset of global column gc (height sums first, then the header)
@@ -393,15 +392,6 @@ __device__ __forceinline__ float rule_value_t(const LayerDev& L, float old, floa
   return (r.obs ? old : L.alpha0) + S;  // DIRICHLET
 }
 
-struct __align__(16) ChunkDesc {  // up to four consecutive channels of one source staged together
-  const void* data;
-  int C, ch0;       // row length, first channel
-  int col, n;       // first stage column, channels
-  int dtype, vec;   // storage, 16-byte aligned rows
-  int am;           // arg-max value column of the source (-1: none); bit 30: last chunk
-  int pad;          // source
-  int unused[2];
-};
 
 struct SumSmem {
   u32 key[kFT + 2];  // key[i + 1]: point i; key[0]: the point before the tile; key[np + 1]: after it
@@ -418,10 +408,20 @@ struct SumSmem {
   int n_ck;
   SrcDev src[kMaxSources];
   MapCall mc0;
+  u32 rkey[kFT];     // per run: cell, pre-call accepted / rejected counts, 1 / points
+  u32 na0[kFT], nr0[kFT];
+  float rN[kFT];
+  u32 cmw[kFT / 32][2];     // per warp: arg-max of its last run's points (value, channel)
+  int cmr[kFT / 32];        //           and that run
+  int qc0[kMaxSources], qch0[kMaxSources], qn[kMaxSources];  // per source: first column,
+                                                             // first channel, channels in the round
+  int pair_col[kMaxSources];  // arg-max value columns of the round
+  int n_pair;
+  LayerDev L[kMaxLayers];
+  int rlay[kMaxSources][kMaxSrcLayers];  // per source: its layers other than class max
+  int nrlay[kMaxSources];
   u32 wcnt[kFT / 32];
   u32 endbits[kFT / 32];  // bit i: point i is the last point of its run in the tile
-  int tile;
-  u32 base;
   int fallback;           // an arg-max pair of the round needs channels of an earlier round
 };
 
@@ -488,21 +488,36 @@ __device__ __forceinline__ void build_columns(SumSmem& s, int n_src, int r0, int
         d.n = 1;
         d.dtype = s.src[q].dtype;
         d.vec = s.src[q].vec_ok;
-        d.pad = q;
+        d.src = q;
       }
     }
     s.n_ck = n;
+    for (int q = 0; q < n_src; ++q) {
+      s.qn[q] = 0;
+      for (int c = 0; c < nr; ++c)
+        if (s.col_src[c] == q && s.col_ch[c] >= 0) {
+          if (s.qn[q] == 0) {
+            s.qc0[q] = c;
+            s.qch0[q] = s.col_ch[c];
+          }
+          ++s.qn[q];
+        }
+    }
     s.fallback = 0;
+    s.n_pair = 0;
     for (int c = 0; c < nr; ++c)
-      if (s.col_ch[c] == kChArgV && slot_off(r0) > s.src[s.col_src[c]].acc_off) s.fallback = 1;
+      if (s.col_ch[c] == kChArgV) {
+        s.pair_col[s.n_pair++] = c;
+        if (slot_off(r0) > s.src[s.col_src[c]].acc_off) s.fallback = 1;
+      }
     // a source whose channels and arg-max pair are all in the round gets its
     // per-point arg-max while it is staged
     for (int k = 0; k < n; ++k) {
-      const int q = s.ck[k].pad;
+      const int q = s.ck[k].src;
       const int first = s.ck[k].col - s.ck[k].ch0;  // column of channel 0
       const int av = first + s.src[q].C;            // arg-max value column
       const bool ok = s.src[q].has_classmax && first >= 0 && av + 1 < nr;
-      const bool last = k + 1 == n || s.ck[k + 1].pad != q;
+      const bool last = k + 1 == n || s.ck[k + 1].src != q;
       s.ck[k].am = ok ? (av | (last ? (1 << 30) : 0)) : -1;
     }
   }
@@ -535,8 +550,133 @@ __device__ __forceinline__ void ld_chunk(const ChunkDesc& d, int64_t row, float 
   for (int w = 0; w < 4; ++w) v[w] = w < d.n ? ld_any(d.data, d.dtype, off + w) : 0.f;
 }
 
-__global__ void __launch_bounds__(kFT, 6) k_fuse_sums(MapDev md, const PointJob* __restrict__ job,
-                                                      int sorted1) {
+
+// (i, j) enumeration of the i-major task list k = i * n + j, k = t, t + kFT, ...
+// without divisions after the first
+struct TaskWalk {
+  int i, j, di, dj, n;
+  __device__ __forceinline__ TaskWalk(int t, int n_) : n(n_) {
+    i = t / n;
+    j = t - i * n;
+    di = kFT / n;
+    dj = kFT - di * n;
+  }
+  __device__ __forceinline__ void next() {
+    i += di;
+    j += dj;
+    if (j >= n) {
+      j -= n;
+      ++i;
+    }
+  }
+};
+
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+// Kalman height update in information form (float32) + cumulative counts.
+__device__ __forceinline__ void height_update(const MapDev& md, u32 g, u32& fl, float h0, float v0, float sw,
+                                              float swz, u32 na, u32 nr, u32 na0, u32 nr0) {
+  float h = h0, v = v0;
+  if (na > 0) {
+    if (fl & kFlagValid) {
+      const float P = __frcp_rn(v0) + sw;
+      h = (h0 * __frcp_rn(v0) + swz) * __frcp_rn(P);
+      v = __frcp_rn(P);
+    } else {
+      h = swz * __frcp_rn(sw);
+      v = __frcp_rn(sw);
+      fl |= kFlagValid;
+    }
+  }
+  if (nr > 0 && md.outlier_var != 0.f) v = fmaf(md.outlier_var, (float)nr, v);
+  md.h[g] = h;
+  md.var[g] = v;
+  md.n_acc[g] = na0 + na;
+  md.n_rej[g] = nr0 + nr;
+}
+
+// class max of a source into its class-max layers
+__device__ __forceinline__ void write_classmax(const LayerDev* Ls, const SrcDev& src, u32 g, float best, int bid) {
+  for (int b = 0; b < src.n_layers; ++b) {
+    const LayerDev& L = Ls[src.layers[b]];
+    if (L.rule == MEM_RULE_CLASSMAX) {
+      float* d = (float*)L.data + (int64_t)g * 2;
+      d[0] = (float)bid;
+      d[1] = best;
+    }
+  }
+}
+
+// Gaussian variances of a source's layers (after every rule read them)
+__device__ __forceinline__ void write_gauss_var(const LayerDev* Ls, const SrcDev& src, u32 g, u32 fl, float N,
+                                                float rN) {
+  for (int b = 0; b < src.n_layers; ++b) {
+    const int l = src.layers[b];
+    const LayerDev& L = Ls[l];
+    if (L.rule != MEM_RULE_GAUSS) continue;
+    const bool obs = fl & (2u << l);
+    L.gvar[g] = rule_coef(L, N, rN, obs, obs ? L.gvar[g] : 0.f).var_new;
+  }
+}
+
+// One rule layer over the runs fused in the tile: tasks (run, channel of the
+// round), kApplyU per thread in flight (old values and Gaussian prior
+// variances first, then the new values). The layer's source channels ch0 ..
+// ch0 + nch - 1 are the stage columns c0 ..
+template <int RULE, int DT>
+__device__ __forceinline__ void tile_rule_t(const SumSmem& s, const LayerDev& Ls, int l, int c0, int ch0, int nch,
+                                            int r_lo, int r_hi) {
+  const LayerDev L = Ls;  // in registers: the stores below cannot alias it
+  const int ntask = (r_hi - r_lo) * nch;
+  TaskWalk tw(threadIdx.x, nch);
+  for (int k0 = threadIdx.x; k0 < ntask; k0 += kApplyU * kFT) {
+    float old[kApplyU], s02[kApplyU];
+    TaskWalk tw0 = tw;
+#pragma unroll
+    for (int u = 0; u < kApplyU; ++u) {
+      old[u] = s02[u] = 0.f;
+      if (k0 + u * kFT < ntask) {
+        const int r = r_lo + tw.i;
+        const u32 g = s.rkey[r];
+        if (s.fl[r] & (2u << l)) {
+          if (RULE != MEM_RULE_LATEST) old[u] = ld1t<DT>(L.data, (int64_t)g * L.S + ch0 + tw.j);
+          if (RULE == MEM_RULE_GAUSS) s02[u] = L.gvar[g];
+        }
+      }
+      tw.next();
+    }
+#pragma unroll
+    for (int u = 0; u < kApplyU; ++u) {
+      if (k0 + u * kFT < ntask) {
+        const int r = r_lo + tw0.i;
+        const RuleCoef co = rule_coef(L, (float)(s.rstart[r + 1] - s.rstart[r]), s.rN[r],
+                                      (s.fl[r] & (2u << l)) != 0, s02[u]);
+        st1t<DT>(L.data, (int64_t)s.rkey[r] * L.S + ch0 + tw0.j,
+                 rule_value_t<RULE>(L, old[u], s.stage[s.rstart[r] * kQS + c0 + tw0.j], co));
+      }
+      tw0.next();
+    }
+  }
+}
+
+__device__ __forceinline__ void tile_rule(const SumSmem& s, const LayerDev& L, int l, int c0, int ch0, int nch,
+                                          int r_lo, int r_hi) {
+#define MEM_TR(R, D) \
+  case R * 4 + D: tile_rule_t<R, D>(s, L, l, c0, ch0, nch, r_lo, r_hi); break;
+  switch (L.rule * 4 + L.dtype) {
+    MEM_TR(MEM_RULE_LATEST, MEM_F32) MEM_TR(MEM_RULE_LATEST, MEM_BF16) MEM_TR(MEM_RULE_LATEST, MEM_F16)
+    MEM_TR(MEM_RULE_EXPAVG, MEM_F32) MEM_TR(MEM_RULE_EXPAVG, MEM_BF16) MEM_TR(MEM_RULE_EXPAVG, MEM_F16)
+    MEM_TR(MEM_RULE_GAUSS, MEM_F32) MEM_TR(MEM_RULE_GAUSS, MEM_BF16) MEM_TR(MEM_RULE_GAUSS, MEM_F16)
+    MEM_TR(MEM_RULE_DIRICHLET, MEM_F32)
+    default: break;
+  }
+#undef MEM_TR
+}
+
+__global__ void __launch_bounds__(kFT, 6) k_fuse_tiles(MapDev md, const PointJob* __restrict__ job,
+                                                       int sorted1) {
   extern __shared__ __align__(16) unsigned char fz_raw[];
   SumSmem& s = *reinterpret_cast<SumSmem*>(fz_raw);
   const u32* __restrict__ sk = sorted1 ? md.keys1 : md.keys0;
@@ -545,20 +685,38 @@ __global__ void __launch_bounds__(kFT, 6) k_fuse_sums(MapDev md, const PointJob*
   const int n_tiles = (int)((n_kept + kFT - 1) / kFT);
   const int n_src = job->n_src;
   const int acc = job->acc;
-  const int G = acc - (kSlotHdr - 4);  // global columns
+  const FuseTables* __restrict__ ft = &job->ft;
+  const int G = ft->ncol;  // columns of the call
+  const bool one_round = ft->one_round;
+  const bool any_gauss = ft->any_gauss;  // Gaussian variances are written after every rule read them
   const float* __restrict__ xyz = job->xyz;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  // the call's tables (built on the host) into shared memory
   if (t < n_src) s.src[t] = job->src[t];
+  if (t < md.n_layers) s.L[t] = md.L[t];
   if (t == 0) s.mc0 = job->maps[0];
-  __syncthreads();
-  const bool one_round = round_end(s.src, n_src, 0, G) == G;
-  if (one_round) build_columns(s, n_src, 0, G);
-  for (;;) {
+  if (t < kMaxSources) {
+    s.nrlay[t] = ft->nrlay[t];
+    for (int b = 0; b < kMaxSrcLayers; ++b) s.rlay[t][b] = ft->rlay[t][b];
+    s.qc0[t] = ft->qc0[t];
+    s.qch0[t] = ft->qch0[t];
+    s.qn[t] = ft->qn[t];
+    s.pair_col[t] = ft->pair_col[t];
+  }
+  if (one_round) {
+    for (int i = t; i < kQ; i += kFT) {
+      s.col_src[i] = ft->col_src[i];
+      s.col_ch[i] = ft->col_ch[i];
+      s.ck[i] = ft->ck[i];
+    }
+    if (t == 0) {
+      s.n_ck = ft->n_ck;
+      s.n_pair = ft->n_pair;
+      s.fallback = 0;
+    }
+  }
+  for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
     __syncthreads();  // the previous tile is done with the shared arrays
-    if (t == 0) s.tile = atomicAdd(&md.counters[7], 1);
-    __syncthreads();
-    const int tile = s.tile;
-    if (tile >= n_tiles) break;
     const int64_t p0 = (int64_t)tile * kFT;
     const int np = (int)min((int64_t)kFT, n_kept - p0);
     // A. keys, point indices, runs
@@ -587,40 +745,57 @@ __global__ void __launch_bounds__(kFT, 6) k_fuse_sums(MapDev md, const PointJob*
     }
     const int myrun = rbase + __popc(bal & ((2u << lane) - 1u)) - 1;
     if (t < np) s.pinf[t] = (myrun << 1) | (ed ? 1 : 0);
-    if (hd) s.rstart[myrun] = t;
-    if (t == 0) {
-      s.rstart[nruns] = np;
-      s.base = atomicAdd(&md.counters[8], (u32)nruns);
+    if (hd) {
+      s.rstart[myrun] = t;
+      s.rkey[myrun] = s.key[t + 1];
     }
+    if (t == 0) s.rstart[nruns] = np;
+    const int rl = nruns - 1;
+    const bool gh0 = s.key[0] != s.key[1];        // run 0 begins in this tile
+    const bool geL = s.key[np] != s.key[np + 1];  // the last run ends in this tile
+    const int r_lo = gh0 ? 0 : 1, r_hi = geL ? nruns : rl;  // runs fused here
+    // pieces carried to slots: a first run begun earlier that ends here ([0]);
+    // a last run that continues past the tile ([1], also when it is the only run)
+    float* cin = (!gh0 && (nruns > 1 || geL)) ? fz_slot(md, acc, tile, 0) : nullptr;
+    float* cout = !geL ? fz_slot(md, acc, tile, 1) : nullptr;
     __syncthreads();
-    const u32 base = s.base;
-    if (t == 0) {
-      fz_tile_base(md)[tile] = base;
-      fz_tile_runs(md)[tile] = (u32)nruns;
-    }
-    // B. pre-call state of every run's cell into the slot header (and the
-    //    gate's part to shared memory), coordinates of every point
+    // B. pre-call state of every run's cell; slot headers of the carried
+    //    pieces; the rule layers' rows of the cells into L2; coordinates
     if (t < nruns) {
-      const int i0 = s.rstart[t], i1 = s.rstart[t + 1];
-      const u32 g = s.key[i0 + 1];
+      const u32 g = s.rkey[t];
       const u32 fl = md.flags[g];
       const float h0 = md.h[g], v0 = md.var[g];
       const u32 na = md.n_acc[g], nr = md.n_rej[g];
       s.fl[t] = fl;
       s.h0[t] = h0;
       s.v0[t] = v0;
-      float* hdr = fz_slot(md, acc, base + t);
-      const u32 bits = (i0 > 0 || s.key[0] != s.key[1] ? kBitHead : 0u) |
-                       (i1 < np || s.key[np] != s.key[np + 1] ? kBitEnd : 0u);
-      hdr[kSlotKey] = __uint_as_float(g);
-      hdr[kSlotN] = __uint_as_float((u32)(i1 - i0));
-      hdr[kSlotBits] = __uint_as_float(bits);
-      hdr[kSlotFl] = __uint_as_float(fl);
-      hdr[kSlotH0] = h0;
-      hdr[kSlotV0] = v0;
-      hdr[kSlotNacc] = __uint_as_float(na);
-      hdr[kSlotNrej] = __uint_as_float(nr);
+      s.na0[t] = na;
+      s.nr0[t] = nr;
+      s.rN[t] = __frcp_rn((float)(s.rstart[t + 1] - s.rstart[t]));
+      float* hdr = (t == 0 && cin) ? cin : (t == rl && cout) ? cout : nullptr;
+      if (hdr) {
+        const u32 bits = kBitUsed | (t > 0 || gh0 ? kBitHead : 0u) | (t < rl || geL ? kBitEnd : 0u);
+        hdr[kSlotKey] = __uint_as_float(g);
+        hdr[kSlotN] = __uint_as_float((u32)(s.rstart[t + 1] - s.rstart[t]));
+        hdr[kSlotBits] = __uint_as_float(bits);
+        hdr[kSlotFl] = __uint_as_float(fl);
+        hdr[kSlotH0] = h0;
+        hdr[kSlotV0] = v0;
+        hdr[kSlotNacc] = __uint_as_float(na);
+        hdr[kSlotNrej] = __uint_as_float(nr);
+      }
+      for (int q = 0; q < n_src; ++q)
+        for (int j = 0; j < s.nrlay[q]; ++j) {
+          const LayerDev& L = s.L[s.rlay[q][j]];
+          if (L.rule == MEM_RULE_LATEST) continue;
+          const int bytes = L.S * (L.dtype == MEM_F32 ? 4 : 2);
+          const char* row = (const char*)L.data + (int64_t)g * bytes;
+          for (int o = 0; o < bytes; o += 128) prefetch_l2(row + o);
+          prefetch_l2(row + bytes - 1);
+        }
     }
+    if (t == 0 && !cin) fz_slot(md, acc, tile, 0)[kSlotBits] = 0.f;  // unused this call
+    if (t == 0 && !cout) fz_slot(md, acc, tile, 1)[kSlotBits] = 0.f;
     float xs = 0.f, ys = 0.f, zs = 0.f;
     if (t < np) {
       const int64_t id = s.idx[t];
@@ -709,17 +884,47 @@ __global__ void __launch_bounds__(kFT, 6) k_fuse_sums(MapDev md, const PointJob*
         }
       }
       __syncthreads();
-      // walk: thread (segment, column) over the segment's points in order; an
-      // arg-max column carries (value, channel) pairs from its column and the next
+      // class max per run of every arg-max pair of the round: segmented max of
+      // (value, channel) over each warp's points (runs are contiguous), then
+      // the run's last point adds the tails of earlier warps the run covers;
+      // the run's result goes to its first row
+      for (int pc = 0; pc < s.n_pair; ++pc) {
+        const int c = s.pair_col[pc];
+        const int run = t < np ? s.pinf[t] >> 1 : -1 - warp;
+        float2 m = t < np ? make_float2(s.stage[t * kQS + c], s.stage[t * kQS + c + 1])
+                          : make_float2(-INFINITY, __int_as_float(0x7fffffff));
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const float ov = __shfl_up_sync(0xffffffffu, m.x, o);
+          const float oi = __shfl_up_sync(0xffffffffu, m.y, o);
+          const int orun = __shfl_up_sync(0xffffffffu, run, o);
+          if (lane >= o && orun == run) m = cm_comb(make_float2(ov, oi), m);
+        }
+        if (lane == 31) {
+          s.cmw[warp][0] = __float_as_uint(m.x);
+          s.cmw[warp][1] = __float_as_uint(m.y);
+          s.cmr[warp] = run;
+        }
+        __syncthreads();
+        if (t < np && (s.pinf[t] & 1)) {
+          for (int w = warp - 1; w >= 0 && s.cmr[w] == run; --w)
+            m = cm_comb(make_float2(__uint_as_float(s.cmw[w][0]), __uint_as_float(s.cmw[w][1])), m);
+          float* row = s.stage + s.rstart[run] * kQS + c;
+          row[0] = m.x;
+          row[1] = m.y;
+        }
+        __syncthreads();
+      }
+      // walk: thread (segment, column) over the segment's points in order
+      // (height sums and source channels; the arg-max pairs are done)
       {
         const int nseg = max(1, min(min(kFT / nr, kSegMax), np));
         const int len = (np + nseg - 1) / nseg;
         const int sg = t / nr, c = t - sg * nr;
         const int i0 = sg * len, i1 = min(i0 + len, np);
-        const bool on = sg < nseg && i0 < i1 && s.col_ch[c] != kChArgI;
-        const bool pair = on && s.col_ch[c] == kChArgV;
+        const bool on = sg < nseg && i0 < i1 && (s.col_src[c] < 0 || s.col_ch[c] >= 0);
         const bool cont0 = on && i0 > 0 && !((s.endbits[(i0 - 1) >> 5] >> ((i0 - 1) & 31)) & 1u);
-        if (on && !pair) {
+        if (on) {
           // run ends of the segment as a bit mask; values eight at a time
           const int n = i1 - i0;
           const int wb = i0 >> 5, ob = i0 & 31;
@@ -748,25 +953,6 @@ __global__ void __launch_bounds__(kFT, 6) k_fuse_sums(MapDev md, const PointJob*
             }
           }
           if (!((em >> (n - 1)) & 1u)) s.tp[sg * nr + c].x = a;
-        } else if (pair) {
-          bool cont = cont0;
-          float2 m = make_float2(-INFINITY, __int_as_float(0x7fffffff));
-          for (int i = i0; i < i1; ++i) {
-            m = cm_comb(m, make_float2(s.stage[i * kQS + c], s.stage[i * kQS + c + 1]));
-            const int pf = s.pinf[i];
-            if (pf & 1) {
-              if (cont) {
-                s.hp[sg * nr + c] = m;
-              } else {
-                float* row = s.stage + s.rstart[pf >> 1] * kQS + c;
-                row[0] = m.x;
-                row[1] = m.y;
-              }
-              cont = false;
-              m = make_float2(-INFINITY, __int_as_float(0x7fffffff));
-            }
-          }
-          if (!(s.pinf[i1 - 1] & 1)) s.tp[sg * nr + c] = m;
         }
         __syncthreads();
         // runs that cross segments: finished by the segment holding their last point
@@ -774,271 +960,153 @@ __global__ void __launch_bounds__(kFT, 6) k_fuse_sums(MapDev md, const PointJob*
           const int r = s.pinf[i0] >> 1;
           if (s.rstart[r + 1] <= i1) {
             const int s0 = s.rstart[r] / len;
-            float* row = s.stage + s.rstart[r] * kQS + c;
-            if (!pair) {
-              float a = s.tp[s0 * nr + c].x;
-              for (int k = s0 + 1; k < sg; ++k) a += s.tp[k * nr + c].x;
-              row[0] = a + s.hp[sg * nr + c].x;
-            } else {
-              float2 a = s.tp[s0 * nr + c];
-              for (int k = s0 + 1; k < sg; ++k) a = cm_comb(a, s.tp[k * nr + c]);
-              a = cm_comb(a, s.hp[sg * nr + c]);
-              row[0] = a.x;
-              row[1] = a.y;
-            }
+            float a = s.tp[s0 * nr + c].x;
+            for (int k = s0 + 1; k < sg; ++k) a += s.tp[k * nr + c].x;
+            s.stage[s.rstart[r] * kQS + c] = a + s.hp[sg * nr + c].x;
           }
         }
         __syncthreads();
       }
-      // run sums of the round to the slots: tasks (run, column)
-      {
-        int r = t / nr, c = t - (t / nr) * nr;
-        const int dr = kFT / nr, dc = kFT - dr * nr;
-        for (int k = t; k < nruns * nr; k += kFT) {
-          fz_slot(md, acc, base + r)[slot_off(r0 + c)] = s.stage[s.rstart[r] * kQS + c];
-          r += dr;
-          c += dc;
-          if (c >= nr) {
-            c -= nr;
-            ++r;
+      // D. sums of the carried pieces to their slots (nr <= 32: warp 0)
+      if (t < nr) {
+        if (cin) cin[slot_off(r0 + t)] = s.stage[s.rstart[0] * kQS + t];
+        if (cout) cout[slot_off(r0 + t)] = s.stage[s.rstart[rl] * kQS + t];
+      }
+      // E. rules of the runs fused here, layer by layer
+      for (int q = 0; q < n_src; ++q)
+        if (s.qn[q] > 0)
+          for (int j = 0; j < s.nrlay[q]; ++j) {
+            const int l = s.rlay[q][j];
+            tile_rule(s, s.L[l], l, s.qc0[q], s.qch0[q], s.qn[q], r_lo, r_hi);
+          }
+      // F. per run fused here: height update (first round), class max of the
+      //    arg-max pairs of the round (the valid bit joins the flags kept in
+      //    shared memory; rules only read the observed bits)
+      if (t >= r_lo && t < r_hi) {
+        const float* row = s.stage + s.rstart[t] * kQS;
+        const u32 g = s.rkey[t];
+        if (r0 == 0) {
+          u32 fl = s.fl[t];
+          height_update(md, g, fl, s.h0[t], s.v0[t], row[0], row[1], (u32)row[2], (u32)row[3], s.na0[t], s.nr0[t]);
+          s.fl[t] = fl;
+        }
+        for (int q = 0; q < n_src; ++q) {
+          const int av = s.src[q].acc_off - (kSlotHdr - 4) + s.src[q].C - r0;  // arg-max value column in the round
+          if (s.src[q].has_classmax && av >= 0 && av + 1 < nr) {
+            const float best = row[av];
+            write_classmax(s.L, s.src[q], g, best, best == -INFINITY ? -1 : __float_as_int(row[av + 1]));
           }
         }
       }
       r0 = re;
       __syncthreads();  // the next round overwrites the stage
     }
+    // G. Gaussian variances and flags of the runs fused here
+    if (t >= r_lo && t < r_hi) {
+      const u32 g = s.rkey[t];
+      u32 fl = s.fl[t];
+      const float N = (float)(s.rstart[t + 1] - s.rstart[t]);
+      for (int q = 0; q < n_src; ++q) {
+        if (any_gauss) write_gauss_var(s.L, s.src[q], g, fl, N, __frcp_rn(N));
+        for (int b = 0; b < s.src[q].n_layers; ++b) fl |= 2u << s.src[q].layers[b];
+      }
+      md.flags[g] = fl;
+    }
+    if (t == 0) {
+      const u32 heads = (u32)(nruns - (gh0 ? 0 : 1));
+      if (heads) atomicAdd(&md.counters[5], heads);
+    }
   }
 }
 
 // ---------------------------------------------------------------------------
 
-struct ApplySmem {
-  u32 base[kFT];  // per run: slot, cell, flags, first following tile (0: the run ends here)
-  u32 g[kFT];
-  u32 fl[kFT];
-  int cont[kFT];
-  float N[kFT], rN[kFT];  // observations of the cell in this call
-  LayerDev L[kMaxLayers];
-  SrcDev src[kMaxSources];
-  int tile;
-};
-
-// value at slot offset o, summed over the run's slot and its continuations
-// (in tile order)
-__device__ __forceinline__ float run_sum(const MapDev& md, int acc, u32 slot, int cont, int n_tiles, int o) {
-  float S = __ldcg(fz_slot(md, acc, slot) + o);
-  for (int tt = cont; tt > 0 && tt < n_tiles; ++tt) {
-    const float* sl = fz_slot(md, acc, fz_tile_base(md)[tt]);
-    S += __ldcg(sl + o);
-    if (__float_as_uint(__ldcg(sl + kSlotBits)) & kBitEnd) break;
-  }
-  return S;
-}
-
-// One rule layer over tasks (run, channel) of the tile's runs, kApplyU tasks
-// per thread in flight (old values, prior variances and sums first).
-template <int RULE, int DT>
-__device__ __forceinline__ void apply_layer_t(const MapDev& md, const ApplySmem& s, const LayerDev& L, int l,
-                                              int o0, int nruns, int acc, int n_tiles) {
-  const int C = L.C, ntask = nruns * C;
-  int r = threadIdx.x / C, c = threadIdx.x - (threadIdx.x / C) * C;
-  const int dr = kFT / C, dc = kFT - dr * C;
-  for (int k0 = threadIdx.x; k0 < ntask; k0 += kApplyU * kFT) {
-    float old[kApplyU], s02[kApplyU], S[kApplyU];
-    int rr[kApplyU], cc[kApplyU];
-#pragma unroll
-    for (int u = 0; u < kApplyU; ++u) {
-      rr[u] = r;
-      cc[u] = c;
-      old[u] = s02[u] = S[u] = 0.f;
-      if (k0 + u * kFT < ntask) {
-        const u32 g = s.g[r];
-        if (s.fl[r] & (2u << l)) {
-          if (RULE != MEM_RULE_LATEST) old[u] = ld1t<DT>(L.data, (int64_t)g * L.S + c);
-          if (RULE == MEM_RULE_GAUSS) s02[u] = L.gvar[g];
-        }
-        S[u] = run_sum(md, acc, s.base[r], s.cont[r], n_tiles, o0 + c);
-      }
-      r += dr;
-      c += dc;
-      if (c >= C) {
-        c -= C;
-        ++r;
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < kApplyU; ++u) {
-      if (k0 + u * kFT < ntask) {
-        const int q = rr[u];
-        const bool obs = s.fl[q] & (2u << l);
-        const RuleCoef co = rule_coef(L, s.N[q], s.rN[q], obs, s02[u]);
-        st1t<DT>(L.data, (int64_t)s.g[q] * L.S + cc[u], rule_value_t<RULE>(L, old[u], S[u], co));
-      }
-    }
-  }
-}
-
-__device__ __forceinline__ void apply_layer(const MapDev& md, const ApplySmem& s, const LayerDev& L, int l, int o0,
-                                            int nruns, int acc, int n_tiles) {
-#define MEM_AL(R, D) \
-  case R * 4 + D: apply_layer_t<R, D>(md, s, L, l, o0, nruns, acc, n_tiles); break;
-  switch (L.rule * 4 + L.dtype) {
-    MEM_AL(MEM_RULE_LATEST, MEM_F32) MEM_AL(MEM_RULE_LATEST, MEM_BF16) MEM_AL(MEM_RULE_LATEST, MEM_F16)
-    MEM_AL(MEM_RULE_EXPAVG, MEM_F32) MEM_AL(MEM_RULE_EXPAVG, MEM_BF16) MEM_AL(MEM_RULE_EXPAVG, MEM_F16)
-    MEM_AL(MEM_RULE_GAUSS, MEM_F32) MEM_AL(MEM_RULE_GAUSS, MEM_BF16) MEM_AL(MEM_RULE_GAUSS, MEM_F16)
-    MEM_AL(MEM_RULE_DIRICHLET, MEM_F32)
-    default: break;
-  }
-#undef MEM_AL
-}
-
-__device__ __forceinline__ void prefetch_l2(const void* p) {
-  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-}
-
-__global__ void __launch_bounds__(kFT) k_fuse_apply(MapDev md, const PointJob* __restrict__ job) {
-  __shared__ ApplySmem s;
+// One warp per run that crosses tile boundaries, started from the tile where
+// it begins: the pieces are that tile's slot [1], the slots [1] of the tiles
+// it covers entirely, and slot [0] of the tile where it ends (found by lanes
+// reading 32 tiles' slot bits at once); lanes then take columns.
+__global__ void __launch_bounds__(128) k_fuse_cross(MapDev md, const PointJob* __restrict__ job) {
+  __shared__ LayerDev sL[kMaxLayers];
+  __shared__ SrcDev ssrc[kMaxSources];
   const int64_t n_kept = *(volatile u32*)&md.counters[6];
   const int n_tiles = (int)((n_kept + kFT - 1) / kFT);
   const int n_src = job->n_src;
   const int acc = job->acc;
-  const int t = threadIdx.x;
-  if (t < md.n_layers) s.L[t] = md.L[t];
-  if (t < n_src) s.src[t] = job->src[t];
+  const int G = job->ft.ncol;
+  if (threadIdx.x < md.n_layers) sL[threadIdx.x] = md.L[threadIdx.x];
+  if (threadIdx.x < n_src) ssrc[threadIdx.x] = job->src[threadIdx.x];
   __syncthreads();
-  bool any_gauss = false;  // Gaussian variances are written after every rule read them
-  for (int q = 0; q < n_src; ++q)
-    for (int b = 0; b < s.src[q].n_layers; ++b) any_gauss |= s.L[s.src[q].layers[b]].rule == MEM_RULE_GAUSS;
-  for (;;) {
-    __syncthreads();  // the previous tile is done with the shared arrays
-    if (t == 0) s.tile = atomicAdd(&md.counters[9], 1);
-    __syncthreads();
-    const int tile = s.tile;
-    if (tile >= n_tiles) break;
-    const u32 tb = fz_tile_base(md)[tile];
-    const int tr = (int)fz_tile_runs(md)[tile];
-    // runs that begin in this tile: all but a first run carried in
-    const int r_lo = (__float_as_uint(__ldcg(fz_slot(md, acc, tb) + kSlotBits)) & kBitHead) ? 0 : 1;
-    const int nruns = tr - r_lo;
-    // per run: totals over the run's slots, height update, class max, flags;
-    // the rule layers' rows are prefetched into L2 for the passes below
-    if (t < nruns) {
-      const u32 slot = tb + r_lo + t;
-      const float* hdr = fz_slot(md, acc, slot);
-      float sw = __ldcg(hdr), swz = __ldcg(hdr + 1);
-      u32 na = (u32)__ldcg(hdr + 2), nr = (u32)__ldcg(hdr + 3);
-      u32 n = __float_as_uint(__ldcg(hdr + kSlotN));
-      const u32 g = __float_as_uint(__ldcg(hdr + kSlotKey));
-      const u32 fl0 = __float_as_uint(__ldcg(hdr + kSlotFl));
-      for (int q = 0; q < n_src; ++q) {
-        const SrcDev& src = s.src[q];
+  const int lane = threadIdx.x & 31;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  u32 crossing = 0;
+  for (int h = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; h < n_tiles; h += nwarps) {
+    const float* head = fz_slot(md, acc, h, 1);
+    const u32 hb = __float_as_uint(__ldcg(head + kSlotBits));
+    if ((hb & (kBitUsed | kBitHead)) != (kBitUsed | kBitHead)) continue;  // warp-uniform
+    ++crossing;
+    // the tile where the run ends: the first following tile whose slot [0] is used
+    int last = -1;
+    for (int t0 = h + 1; last < 0 && t0 < n_tiles; t0 += 32) {
+      const int tt = t0 + lane;
+      const bool end = tt < n_tiles && (__float_as_uint(__ldcg(fz_slot(md, acc, tt, 0) + kSlotBits)) & kBitUsed);
+      const u32 m = __ballot_sync(0xffffffffu, end);
+      if (m) last = t0 + __ffs(m) - 1;
+    }
+    if (last < 0) last = n_tiles - 1;  // not reached for a consistent slot table
+    // header of the run (the pre-call state is the same in every piece)
+    const u32 g = __float_as_uint(__ldcg(head + kSlotKey));
+    const u32 fl0 = __float_as_uint(__ldcg(head + kSlotFl));
+    u32 n = 0;
+    for (int tt = h; tt <= last; ++tt) n += __float_as_uint(__ldcg(fz_slot(md, acc, tt, tt == last ? 0 : 1) + kSlotN));
+    const float N = (float)n, rN = __frcp_rn(N);
+    // columns: lanes add the pieces in tile order, then fuse their channels
+    float hsum[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int c0 = 0; c0 < G; c0 += 32) {
+      const int gc = c0 + lane;
+      float S = 0.f;
+      float2 m = make_float2(-INFINITY, __int_as_float(0x7fffffff));
+      int q = -1, ch = gc;
+      if (gc < G && gc >= 4) col_ident(ssrc, n_src, gc, q, ch);
+      if (gc < G) {
+        for (int tt = h; tt <= last; ++tt) {
+          const float* sl = fz_slot(md, acc, tt, tt == last ? 0 : 1);
+          const float v = __ldcg(sl + slot_off(gc));
+          S += v;
+          if (ch == kChArgV) m = cm_comb(m, make_float2(v, __ldcg(sl + slot_off(gc) + 1)));
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float hv = __shfl_sync(0xffffffffu, S, k);
+        if (c0 == 0) hsum[k] = hv;
+      }
+      if (q >= 0 && ch >= 0) {
+        const SrcDev& src = ssrc[q];
         for (int b = 0; b < src.n_layers; ++b) {
           const int l = src.layers[b];
-          const LayerDev& L = s.L[l];
-          if (L.rule == MEM_RULE_CLASSMAX || L.rule == MEM_RULE_LATEST || !(fl0 & (2u << l))) continue;
-          const char* row = (const char*)L.data + (int64_t)g * L.S * (L.dtype == MEM_F32 ? 4 : 2);
-          const int bytes = L.S * (L.dtype == MEM_F32 ? 4 : 2);
-          for (int o = 0; o < bytes; o += 128) prefetch_l2(row + o);
-          prefetch_l2(row + bytes - 1);
+          const LayerDev& L = sL[l];
+          if (L.rule == MEM_RULE_CLASSMAX) continue;
+          const bool obs = fl0 & (2u << l);
+          const float s02 = (L.rule == MEM_RULE_GAUSS && obs) ? L.gvar[g] : 0.f;
+          apply_rule(L, (int64_t)g * L.S + ch, S, rule_coef(L, N, rN, obs, s02));
         }
       }
-      int cont = 0;
-      if (!(__float_as_uint(__ldcg(hdr + kSlotBits)) & kBitEnd)) {
-        // the run continues: add the following tiles' first pieces
-        cont = tile + 1;
-        for (int tt = tile + 1; tt < n_tiles; ++tt) {
-          const float* sl = fz_slot(md, acc, fz_tile_base(md)[tt]);
-          sw += __ldcg(sl);
-          swz += __ldcg(sl + 1);
-          na += (u32)__ldcg(sl + 2);
-          nr += (u32)__ldcg(sl + 3);
-          n += __float_as_uint(__ldcg(sl + kSlotN));
-          if (__float_as_uint(__ldcg(sl + kSlotBits)) & kBitEnd) break;
-        }
-      }
-      const float N = (float)n, rN = __frcp_rn((float)n);
-      s.base[t] = slot;
-      s.g[t] = g;
-      s.fl[t] = fl0;
-      s.cont[t] = cont;
-      s.N[t] = N;
-      s.rN[t] = rN;
-      // Kalman height update in information form (float32) + cumulative counts
+      if (q >= 0 && ch == kChArgV) write_classmax(sL, ssrc[q], g, m.x, m.x == -INFINITY ? -1 : __float_as_int(m.y));
+    }
+    __syncwarp();  // every rule read its Gaussian prior variance
+    if (lane == 0) {
       u32 fl = fl0;
-      const float h0 = __ldcg(hdr + kSlotH0), v0 = __ldcg(hdr + kSlotV0);
-      float h = h0, v = v0;
-      if (na > 0) {
-        if (fl & kFlagValid) {
-          const float P = __frcp_rn(v0) + sw;
-          h = (h0 * __frcp_rn(v0) + swz) * __frcp_rn(P);
-          v = __frcp_rn(P);
-        } else {
-          h = swz * __frcp_rn(sw);
-          v = __frcp_rn(sw);
-          fl |= kFlagValid;
-        }
-      }
-      if (nr > 0 && md.outlier_var != 0.f) v = fmaf(md.outlier_var, (float)nr, v);
-      md.h[g] = h;
-      md.var[g] = v;
-      md.n_acc[g] = __float_as_uint(__ldcg(hdr + kSlotNacc)) + na;
-      md.n_rej[g] = __float_as_uint(__ldcg(hdr + kSlotNrej)) + nr;
-      // class max; then every bound layer is observed
+      height_update(md, g, fl, __ldcg(head + kSlotH0), __ldcg(head + kSlotV0), hsum[0], hsum[1], (u32)hsum[2],
+                    (u32)hsum[3], __float_as_uint(__ldcg(head + kSlotNacc)),
+                    __float_as_uint(__ldcg(head + kSlotNrej)));
       for (int q = 0; q < n_src; ++q) {
-        const SrcDev& src = s.src[q];
-        if (src.has_classmax) {
-          const int o = src.acc_off + src.C;
-          float2 bv = make_float2(__ldcg(hdr + o), __ldcg(hdr + o + 1));
-          for (int tt = cont; tt > 0 && tt < n_tiles; ++tt) {
-            const float* sl = fz_slot(md, acc, fz_tile_base(md)[tt]);
-            bv = cm_comb(bv, make_float2(__ldcg(sl + o), __ldcg(sl + o + 1)));
-            if (__float_as_uint(__ldcg(sl + kSlotBits)) & kBitEnd) break;
-          }
-          const int bid = bv.x == -INFINITY ? -1 : __float_as_int(bv.y);
-          for (int b = 0; b < src.n_layers; ++b) {
-            const LayerDev& L = s.L[src.layers[b]];
-            if (L.rule == MEM_RULE_CLASSMAX) {
-              float* d = (float*)L.data + (int64_t)g * 2;
-              d[0] = (float)bid;
-              d[1] = bv.x;
-            }
-          }
-        }
-        for (int b = 0; b < src.n_layers; ++b) fl |= 2u << src.layers[b];
+        write_gauss_var(sL, ssrc[q], g, fl0, N, rN);
+        for (int b = 0; b < ssrc[q].n_layers; ++b) fl |= 2u << ssrc[q].layers[b];
       }
       md.flags[g] = fl;
     }
-    __syncthreads();
-    // rules, layer by layer (they read the pre-call observed bits kept in shared memory)
-    for (int q = 0; q < n_src; ++q) {
-      const SrcDev& src = s.src[q];
-      for (int b = 0; b < src.n_layers; ++b) {
-        const int l = src.layers[b];
-        if (s.L[l].rule != MEM_RULE_CLASSMAX) apply_layer(md, s, s.L[l], l, src.acc_off, nruns, acc, n_tiles);
-      }
-    }
-    if (any_gauss) {
-      __syncthreads();  // every rule read its Gaussian prior variance
-      if (t < nruns) {
-        const u32 g = s.g[t];
-        const u32 fl = s.fl[t];
-        for (int q = 0; q < n_src; ++q)
-          for (int b = 0; b < s.src[q].n_layers; ++b) {
-            const int l = s.src[q].layers[b];
-            const LayerDev& L = s.L[l];
-            if (L.rule != MEM_RULE_GAUSS) continue;
-            const bool obs = fl & (2u << l);
-            L.gvar[g] = rule_coef(L, s.N[t], s.rN[t], obs, obs ? L.gvar[g] : 0.f).var_new;
-          }
-      }
-    }
-    if (t == 0) {
-      if (nruns) atomicAdd(&md.counters[5], (u32)nruns);
-      u32 crossing = 0;
-      for (int r = 0; r < nruns; ++r) crossing += s.cont[r] != 0;
-      if (crossing) atomicAdd(&md.counters[4], crossing);
-    }
   }
+  if (lane == 0 && crossing) atomicAdd(&md.counters[4], crossing);
 }
 
 // time-dependent variance growth of every valid cell
@@ -1056,8 +1124,8 @@ __global__ void k_time_update(MapDev md, int64_t cells) {
 namespace memh {
 using namespace memk;
 
-// resident CTAs per SM of the fuse kernels (their persistent grids)
-static int g_sums_ctas_per_sm = 1, g_apply_ctas_per_sm = 1;
+// resident CTAs per SM of the tile fuse kernel (its persistent grid)
+static int g_sums_ctas_per_sm = 1;
 
 template <int RB>
 static size_t sort_smem() {
@@ -1095,12 +1163,12 @@ static cudaError_t launch_rb(Map* m, const PointJob* d_job, cudaStream_t st) {
     for (int p = 0; p < P; ++p) k_onesweep<RB><<<sms * 2, kSortThreads, sort_smem<RB>(), st>>>(md, d_job, p);
   }
   {
-    ProfScope ps(m, kProfFuseSums, st);
-    k_fuse_sums<<<sms * g_sums_ctas_per_sm, kFT, sizeof(SumSmem), st>>>(md, d_job, P & 1);
+    ProfScope ps(m, kProfFuseTiles, st);
+    k_fuse_tiles<<<sms * g_sums_ctas_per_sm, kFT, sizeof(SumSmem), st>>>(md, d_job, P & 1);
   }
   {
-    ProfScope ps(m, kProfFuseApply, st);
-    k_fuse_apply<<<sms * g_apply_ctas_per_sm, kFT, 0, st>>>(md, d_job);
+    ProfScope ps(m, kProfFuseCross, st);
+    k_fuse_cross<<<sms * 4, 128, 0, st>>>(md, d_job);
   }
   if (md.time_var != 0.f) {
     ProfScope ps(m, kProfTime, st);
@@ -1111,14 +1179,11 @@ static cudaError_t launch_rb(Map* m, const PointJob* d_job, cudaStream_t st) {
 }
 
 cudaError_t prepare_kernels() {
-  cudaError_t e = cudaFuncSetAttribute(k_fuse_sums, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_fuse_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)sizeof(SumSmem));
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_sums_ctas_per_sm, k_fuse_sums, kFT, sizeof(SumSmem));
-  if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_apply_ctas_per_sm, k_fuse_apply, kFT, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_sums_ctas_per_sm, k_fuse_tiles, kFT, sizeof(SumSmem));
   if (g_sums_ctas_per_sm < 1) g_sums_ctas_per_sm = 1;
-  if (g_apply_ctas_per_sm < 1) g_apply_ctas_per_sm = 1;
   if (e == cudaSuccess) e = set_attrs<8>();
   if (e == cudaSuccess) e = set_attrs<9>();
   if (e == cudaSuccess) e = set_attrs<10>();

@@ -31,7 +31,7 @@ EXPORTS = ["mem_create_map", "mem_destroy_map", "mem_move_map", "mem_fuse_pointc
            "mem_unet_param_count", "mem_unet_set_params", "mem_unet_get_params", "mem_unet_forward",
            "mem_unet_gradients", "mem_unet_train_step"]
 NOALLOC_MAX_POINTS = 1 << 18
-PROFILE_SLOTS = ["key", "digit_scan", "radix_sort", "unused3", "fuse_sums", "fuse_apply",
+PROFILE_SLOTS = ["key", "digit_scan", "radix_sort", "unused3", "fuse_tiles", "fuse_cross",
                  "time_var", "image", "move"]
 
 
