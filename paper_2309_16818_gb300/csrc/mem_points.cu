@@ -621,40 +621,92 @@ __device__ __forceinline__ void write_gauss_var(const LayerDev* Ls, const SrcDev
   }
 }
 
-// One rule layer over the runs fused in the tile: tasks (run, channel of the
-// round), kApplyU per thread in flight (old values and Gaussian prior
-// variances first, then the new values). The layer's source channels ch0 ..
-// ch0 + nch - 1 are the stage columns c0 ..
-template <int RULE, int DT>
+// four consecutive stored values (16-byte aligned for F32, 8-byte for 16-bit types)
+template <int DT>
+__device__ __forceinline__ void ld4t(const void* base, int64_t off, float o[4]) {
+  if (DT == MEM_F32) {
+    const float4 q = *reinterpret_cast<const float4*>((const float*)base + off);
+    o[0] = q.x; o[1] = q.y; o[2] = q.z; o[3] = q.w;
+  } else {
+    const uint2 q = *reinterpret_cast<const uint2*>((const uint16_t*)base + off);
+    float2 a, b;
+    if (DT == MEM_BF16) {
+      a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&q.x));
+      b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&q.y));
+    } else {
+      a = __half22float2(*reinterpret_cast<const __half2*>(&q.x));
+      b = __half22float2(*reinterpret_cast<const __half2*>(&q.y));
+    }
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+  }
+}
+template <int DT>
+__device__ __forceinline__ void st4t(void* base, int64_t off, const float n[4]) {
+  if (DT == MEM_F32) {
+    *reinterpret_cast<float4*>((float*)base + off) = make_float4(n[0], n[1], n[2], n[3]);
+  } else {
+    uint2 q;
+    if (DT == MEM_BF16) {
+      __nv_bfloat162 a = __floats2bfloat162_rn(n[0], n[1]), b = __floats2bfloat162_rn(n[2], n[3]);
+      q.x = *reinterpret_cast<u32*>(&a);
+      q.y = *reinterpret_cast<u32*>(&b);
+    } else {
+      __half2 a = __floats2half2_rn(n[0], n[1]), b = __floats2half2_rn(n[2], n[3]);
+      q.x = *reinterpret_cast<u32*>(&a);
+      q.y = *reinterpret_cast<u32*>(&b);
+    }
+    *reinterpret_cast<uint2*>((uint16_t*)base + off) = q;
+  }
+}
+
+// One rule layer over the runs fused in the tile: tasks (run, group of W
+// channels of the round), kRuleU per thread in flight (old values and
+// Gaussian prior variances first, then the new values). The layer's source
+// channels ch0 .. ch0 + nch - 1 are the stage columns c0 ..; W = 4 needs
+// ch0, nch and the layer's row length to be multiples of 4 (aligned rows).
+template <int RULE, int DT, int W>
 __device__ __forceinline__ void tile_rule_t(const SumSmem& s, const LayerDev& Ls, int l, int c0, int ch0, int nch,
                                             int r_lo, int r_hi) {
+  constexpr int kRuleU = W == 4 ? 2 : 4;
   const LayerDev L = Ls;  // in registers: the stores below cannot alias it
-  const int ntask = (r_hi - r_lo) * nch;
-  TaskWalk tw(threadIdx.x, nch);
-  for (int k0 = threadIdx.x; k0 < ntask; k0 += kApplyU * kFT) {
-    float old[kApplyU], s02[kApplyU];
+  const int nq = nch / W;
+  const int ntask = (r_hi - r_lo) * nq;
+  TaskWalk tw(threadIdx.x, nq);
+  for (int k0 = threadIdx.x; k0 < ntask; k0 += kRuleU * kFT) {
+    float old[kRuleU][W], s02[kRuleU];
     TaskWalk tw0 = tw;
 #pragma unroll
-    for (int u = 0; u < kApplyU; ++u) {
-      old[u] = s02[u] = 0.f;
+    for (int u = 0; u < kRuleU; ++u) {
+      s02[u] = 0.f;
+#pragma unroll
+      for (int w = 0; w < W; ++w) old[u][w] = 0.f;
       if (k0 + u * kFT < ntask) {
         const int r = r_lo + tw.i;
         const u32 g = s.rkey[r];
         if (s.fl[r] & (2u << l)) {
-          if (RULE != MEM_RULE_LATEST) old[u] = ld1t<DT>(L.data, (int64_t)g * L.S + ch0 + tw.j);
+          const int64_t off = (int64_t)g * L.S + ch0 + tw.j * W;
+          if (RULE != MEM_RULE_LATEST) {
+            if (W == 4) ld4t<DT>(L.data, off, old[u]);
+            else old[u][0] = ld1t<DT>(L.data, off);
+          }
           if (RULE == MEM_RULE_GAUSS) s02[u] = L.gvar[g];
         }
       }
       tw.next();
     }
 #pragma unroll
-    for (int u = 0; u < kApplyU; ++u) {
+    for (int u = 0; u < kRuleU; ++u) {
       if (k0 + u * kFT < ntask) {
         const int r = r_lo + tw0.i;
         const RuleCoef co = rule_coef(L, (float)(s.rstart[r + 1] - s.rstart[r]), s.rN[r],
                                       (s.fl[r] & (2u << l)) != 0, s02[u]);
-        st1t<DT>(L.data, (int64_t)s.rkey[r] * L.S + ch0 + tw0.j,
-                 rule_value_t<RULE>(L, old[u], s.stage[s.rstart[r] * kQS + c0 + tw0.j], co));
+        const float* S = s.stage + s.rstart[r] * kQS + c0 + tw0.j * W;
+        float nv[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) nv[w] = rule_value_t<RULE>(L, old[u][w], S[w], co);
+        const int64_t off = (int64_t)s.rkey[r] * L.S + ch0 + tw0.j * W;
+        if (W == 4) st4t<DT>(L.data, off, nv);
+        else st1t<DT>(L.data, off, nv[0]);
       }
       tw0.next();
     }
@@ -663,8 +715,12 @@ __device__ __forceinline__ void tile_rule_t(const SumSmem& s, const LayerDev& Ls
 
 __device__ __forceinline__ void tile_rule(const SumSmem& s, const LayerDev& L, int l, int c0, int ch0, int nch,
                                           int r_lo, int r_hi) {
-#define MEM_TR(R, D) \
-  case R * 4 + D: tile_rule_t<R, D>(s, L, l, c0, ch0, nch, r_lo, r_hi); break;
+  const bool v4 = (L.S & 3) == 0 && (ch0 & 3) == 0 && (nch & 3) == 0;
+#define MEM_TR(R, D)                                                                  \
+  case R * 4 + D:                                                                     \
+    if (v4) tile_rule_t<R, D, 4>(s, L, l, c0, ch0, nch, r_lo, r_hi);                  \
+    else tile_rule_t<R, D, 1>(s, L, l, c0, ch0, nch, r_lo, r_hi);                     \
+    break;
   switch (L.rule * 4 + L.dtype) {
     MEM_TR(MEM_RULE_LATEST, MEM_F32) MEM_TR(MEM_RULE_LATEST, MEM_BF16) MEM_TR(MEM_RULE_LATEST, MEM_F16)
     MEM_TR(MEM_RULE_EXPAVG, MEM_F32) MEM_TR(MEM_RULE_EXPAVG, MEM_BF16) MEM_TR(MEM_RULE_EXPAVG, MEM_F16)
@@ -1023,56 +1079,103 @@ __global__ void __launch_bounds__(kFT, 6) k_fuse_tiles(MapDev md, const PointJob
 
 // One warp per run that crosses tile boundaries, started from the tile where
 // it begins: the pieces are that tile's slot [1], the slots [1] of the tiles
-// it covers entirely, and slot [0] of the tile where it ends (found by lanes
-// reading 32 tiles' slot bits at once); lanes then take columns.
+// it covers entirely, and slot [0] of the tile where it ends. Lanes first
+// read the header words and 32 following tiles' slot bits at once (the end
+// is the first following slot [0] in use), then take columns: each adds its
+// column over the pieces in tile order and loads the old values of the
+// column's layers together, then stores the new values.
 __global__ void __launch_bounds__(128) k_fuse_cross(MapDev md, const PointJob* __restrict__ job) {
   __shared__ LayerDev sL[kMaxLayers];
   __shared__ SrcDev ssrc[kMaxSources];
+  __shared__ int srlay[kMaxSources][kMaxSrcLayers], snrlay[kMaxSources];
   const int64_t n_kept = *(volatile u32*)&md.counters[6];
   const int n_tiles = (int)((n_kept + kFT - 1) / kFT);
   const int n_src = job->n_src;
   const int acc = job->acc;
   const int G = job->ft.ncol;
-  if (threadIdx.x < md.n_layers) sL[threadIdx.x] = md.L[threadIdx.x];
-  if (threadIdx.x < n_src) ssrc[threadIdx.x] = job->src[threadIdx.x];
+  const int t = threadIdx.x;
+  if (t < md.n_layers) sL[t] = md.L[t];
+  if (t < n_src) ssrc[t] = job->src[t];
+  if (t < kMaxSources) {
+    snrlay[t] = job->ft.nrlay[t];
+    for (int b = 0; b < kMaxSrcLayers; ++b) srlay[t][b] = job->ft.rlay[t][b];
+  }
   __syncthreads();
-  const int lane = threadIdx.x & 31;
+  const int lane = t & 31;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   u32 crossing = 0;
-  for (int h = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; h < n_tiles; h += nwarps) {
+  for (int h = (blockIdx.x * blockDim.x + t) >> 5; h < n_tiles; h += nwarps) {
     const float* head = fz_slot(md, acc, h, 1);
-    const u32 hb = __float_as_uint(__ldcg(head + kSlotBits));
+    const u32 hw = lane < kSlotHdr ? __float_as_uint(__ldcg(head + lane)) : 0u;
+    const int t1 = h + 1 + lane;
+    const u32 b0 = t1 < n_tiles ? __float_as_uint(__ldcg(fz_slot(md, acc, t1, 0) + kSlotBits)) : kBitUsed;
+    const u32 hb = __shfl_sync(0xffffffffu, hw, kSlotBits);
     if ((hb & (kBitUsed | kBitHead)) != (kBitUsed | kBitHead)) continue;  // warp-uniform
     ++crossing;
-    // the tile where the run ends: the first following tile whose slot [0] is used
-    int last = -1;
-    for (int t0 = h + 1; last < 0 && t0 < n_tiles; t0 += 32) {
+    // the tile where the run ends
+    u32 em = __ballot_sync(0xffffffffu, (b0 & kBitUsed) != 0u);
+    int last = em ? h + __ffs(em) : -1;
+    for (int t0 = h + 33; last < 0 && t0 < n_tiles; t0 += 32) {  // runs longer than 32 tiles
       const int tt = t0 + lane;
-      const bool end = tt < n_tiles && (__float_as_uint(__ldcg(fz_slot(md, acc, tt, 0) + kSlotBits)) & kBitUsed);
-      const u32 m = __ballot_sync(0xffffffffu, end);
-      if (m) last = t0 + __ffs(m) - 1;
+      em = __ballot_sync(0xffffffffu,
+                         tt < n_tiles && (__float_as_uint(__ldcg(fz_slot(md, acc, tt, 0) + kSlotBits)) & kBitUsed));
+      if (em) last = t0 + __ffs(em) - 1;
     }
     if (last < 0) last = n_tiles - 1;  // not reached for a consistent slot table
-    // header of the run (the pre-call state is the same in every piece)
-    const u32 g = __float_as_uint(__ldcg(head + kSlotKey));
-    const u32 fl0 = __float_as_uint(__ldcg(head + kSlotFl));
+    const int np = last - h + 1;      // pieces
+    const u32 g = __shfl_sync(0xffffffffu, hw, kSlotKey);
+    const u32 fl0 = __shfl_sync(0xffffffffu, hw, kSlotFl);
+    // points of the run over its pieces
     u32 n = 0;
-    for (int tt = h; tt <= last; ++tt) n += __float_as_uint(__ldcg(fz_slot(md, acc, tt, tt == last ? 0 : 1) + kSlotN));
+    for (int p = lane; p < np; p += 32)
+      n += __float_as_uint(__ldcg(fz_slot(md, acc, h + p, h + p == last ? 0 : 1) + kSlotN));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
     const float N = (float)n, rN = __frcp_rn(N);
-    // columns: lanes add the pieces in tile order, then fuse their channels
     float hsum[4] = {0.f, 0.f, 0.f, 0.f};
     for (int c0 = 0; c0 < G; c0 += 32) {
       const int gc = c0 + lane;
-      float S = 0.f;
-      float2 m = make_float2(-INFINITY, __int_as_float(0x7fffffff));
       int q = -1, ch = gc;
       if (gc < G && gc >= 4) col_ident(ssrc, n_src, gc, q, ch);
+      float S = 0.f;
+      float2 m = make_float2(-INFINITY, __int_as_float(0x7fffffff));
+      float old[kApplyU], s02[kApplyU];
+#pragma unroll
+      for (int j = 0; j < kApplyU; ++j) old[j] = s02[j] = 0.f;
       if (gc < G) {
-        for (int tt = h; tt <= last; ++tt) {
-          const float* sl = fz_slot(md, acc, tt, tt == last ? 0 : 1);
-          const float v = __ldcg(sl + slot_off(gc));
-          S += v;
-          if (ch == kChArgV) m = cm_comb(m, make_float2(v, __ldcg(sl + slot_off(gc) + 1)));
+        // four pieces' loads in flight, added in tile order
+        for (int p0 = 0; p0 < np; p0 += 4) {
+          float v[4], w[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            v[u] = 0.f;
+            w[u] = __int_as_float(0x7fffffff);
+            if (p0 + u < np) {
+              const float* sl = fz_slot(md, acc, h + p0 + u, h + p0 + u == last ? 0 : 1) + slot_off(gc);
+              v[u] = __ldcg(sl);
+              if (ch == kChArgV) w[u] = __ldcg(sl + 1);
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            if (p0 + u < np) {
+              S += v[u];
+              if (ch == kChArgV) m = cm_comb(m, make_float2(v[u], w[u]));
+            }
+          }
+        }
+        if (q >= 0 && ch >= 0) {
+#pragma unroll
+          for (int j = 0; j < kApplyU; ++j) {
+            if (j < snrlay[q]) {
+              const int l = srlay[q][j];
+              const LayerDev& L = sL[l];
+              if (fl0 & (2u << l)) {
+                if (L.rule != MEM_RULE_LATEST) old[j] = ld_layer(L, (int64_t)g * L.S + ch);
+                if (L.rule == MEM_RULE_GAUSS) s02[j] = L.gvar[g];
+              }
+            }
+          }
         }
       }
 #pragma unroll
@@ -1081,24 +1184,32 @@ __global__ void __launch_bounds__(128) k_fuse_cross(MapDev md, const PointJob* _
         if (c0 == 0) hsum[k] = hv;
       }
       if (q >= 0 && ch >= 0) {
-        const SrcDev& src = ssrc[q];
-        for (int b = 0; b < src.n_layers; ++b) {
-          const int l = src.layers[b];
+#pragma unroll
+        for (int j = 0; j < kApplyU; ++j) {
+          if (j < snrlay[q]) {
+            const int l = srlay[q][j];
+            const LayerDev& L = sL[l];
+            const bool obs = fl0 & (2u << l);
+            st_layer(L, (int64_t)g * L.S + ch, rule_value(L, old[j], S, rule_coef(L, N, rN, obs, s02[j])));
+          }
+        }
+        for (int j = kApplyU; j < snrlay[q]; ++j) {  // more layers than kept in flight
+          const int l = srlay[q][j];
           const LayerDev& L = sL[l];
-          if (L.rule == MEM_RULE_CLASSMAX) continue;
           const bool obs = fl0 & (2u << l);
-          const float s02 = (L.rule == MEM_RULE_GAUSS && obs) ? L.gvar[g] : 0.f;
-          apply_rule(L, (int64_t)g * L.S + ch, S, rule_coef(L, N, rN, obs, s02));
+          const float s2 = (L.rule == MEM_RULE_GAUSS && obs) ? L.gvar[g] : 0.f;
+          apply_rule(L, (int64_t)g * L.S + ch, S, rule_coef(L, N, rN, obs, s2));
         }
       }
       if (q >= 0 && ch == kChArgV) write_classmax(sL, ssrc[q], g, m.x, m.x == -INFINITY ? -1 : __float_as_int(m.y));
     }
+    const float h0 = __uint_as_float(__shfl_sync(0xffffffffu, hw, kSlotH0));
+    const float v0 = __uint_as_float(__shfl_sync(0xffffffffu, hw, kSlotV0));
+    const u32 nacc0 = __shfl_sync(0xffffffffu, hw, kSlotNacc), nrej0 = __shfl_sync(0xffffffffu, hw, kSlotNrej);
     __syncwarp();  // every rule read its Gaussian prior variance
     if (lane == 0) {
       u32 fl = fl0;
-      height_update(md, g, fl, __ldcg(head + kSlotH0), __ldcg(head + kSlotV0), hsum[0], hsum[1], (u32)hsum[2],
-                    (u32)hsum[3], __float_as_uint(__ldcg(head + kSlotNacc)),
-                    __float_as_uint(__ldcg(head + kSlotNrej)));
+      height_update(md, g, fl, h0, v0, hsum[0], hsum[1], (u32)hsum[2], (u32)hsum[3], nacc0, nrej0);
       for (int q = 0; q < n_src; ++q) {
         write_gauss_var(sL, ssrc[q], g, fl0, N, rN);
         for (int b = 0; b < ssrc[q].n_layers; ++b) fl |= 2u << ssrc[q].layers[b];
@@ -1168,7 +1279,7 @@ static cudaError_t launch_rb(Map* m, const PointJob* d_job, cudaStream_t st) {
   }
   {
     ProfScope ps(m, kProfFuseCross, st);
-    k_fuse_cross<<<sms * 4, 128, 0, st>>>(md, d_job);
+    k_fuse_cross<<<sms * 8, 128, 0, st>>>(md, d_job);
   }
   if (md.time_var != 0.f) {
     ProfScope ps(m, kProfTime, st);
