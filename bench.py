@@ -296,43 +296,46 @@ def run_ours(args):
     gpu_launches = int(sum(launches[k] for k in ("key", "radix_sort", "fuse_tiles", "fuse_cross"))
                        + prof["move"][1])
 
-    # ---- end to end through the public API with host buffers
+    # ---- end to end through the public API with host buffers: every step uploads
+    # its pose's cloud from page-locked host memory (mem_fuse_pointcloud_host; the
+    # library overlaps one step's upload with the previous step's kernels) and
+    # reads the height layer back to the host; one event pair around all steps
     e2e = None
     if not args.no_e2e:
         hx = [torch.from_numpy(s.xyz).pin_memory() for s in c["scans"]]
         hr = [torch.from_numpy(s.rgb).pin_memory() for s in c["scans"]]
         hp = [torch.from_numpy(s.probs).pin_memory() for s in c["scans"]]
-        nmax = max(npts)
-        dx = torch.empty((nmax, 3), dtype=torch.float32, device=dev)
-        dr = torch.empty((nmax, 3), dtype=torch.uint8, device=dev)
-        dp = torch.empty((nmax, 20), dtype=torch.float32, device=dev)
-        hh = torch.empty(W * W, dtype=torch.float32).pin_memory()
-        dh = torch.empty(W * W, dtype=torch.float32, device=dev)
-        eev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-        h2d = d2h = 0
-        for i in range(args.warmup + K):
+        hh = [torch.empty(W * W, dtype=torch.float32).pin_memory() for _ in range(2)]
+        dh = [torch.empty(W * W, dtype=torch.float32, device=dev) for _ in range(2)]
+
+        def e2e_step(i):
             k = i % n_pose
-            n = npts[k]
-            if i >= args.warmup:
-                flush(i)
-                eev[i - args.warmup][0].record(stream)
-            dx[:n].copy_(hx[k], non_blocking=True)
-            dr[:n].copy_(hr[k], non_blocking=True)
-            dp[:n].copy_(hp[k], non_blocking=True)
             m.move(c["poses"][k][:2])
-            m.fuse_pointcloud(dx[:n], c["scans"][k].T, [(dr[:n], [0]), (dp[:n], [1, 2, 3])])
-            m.get_layer(M.LAYER_HEIGHT, out=dh)
-            hh.copy_(dh, non_blocking=True)
-            if i >= args.warmup:
-                eev[i - args.warmup][1].record(stream)
-                h2d += n * (12 + 3 + 80)
-                d2h += W * W * 4
+            m.fuse_pointcloud_host(hx[k], c["scans"][k].T, [(hr[k], [0]), (hp[k], [1, 2, 3])])
+            m.get_layer(M.LAYER_HEIGHT, out=dh[i & 1])
+            hh[i & 1].copy_(dh[i & 1], non_blocking=True)
+
+        for i in range(args.warmup):
+            e2e_step(i)
         torch.cuda.synchronize()
-        e_s = max_over_ranks(sum(a.elapsed_time(b) for a, b in eev) / 1e3, ws)
-        e_pts = ws * sum(npts[i % n_pose] for i in range(args.warmup, args.warmup + K))
-        e2e = {"value": round(e_pts / e_s, 1), "unit": UNIT, "h2d_bytes_per_step": int(h2d / K),
+        ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        h2d = d2h = 0
+        e_pts = 0
+        ea.record(stream)
+        for i in range(args.warmup, args.warmup + K):
+            e2e_step(i)
+            n = npts[i % n_pose]
+            e_pts += n
+            h2d += n * (12 + 3 + 80)
+            d2h += W * W * 4
+        eb.record(stream)
+        torch.cuda.synchronize()
+        e_s = max_over_ranks(ea.elapsed_time(eb) / 1e3, ws)
+        e2e = {"value": round(ws * e_pts / e_s, 1), "unit": UNIT, "h2d_bytes_per_step": int(h2d / K),
                "d2h_bytes_per_step": int(d2h / K),
-               "note": "pinned host cloud -> device, move + fuse, height layer -> pinned host"}
+               "note": "mem_fuse_pointcloud_host: page-locked host cloud uploaded each step (10 poses, "
+                       "540 MB of distinct host data cycled), move + fuse, height layer read back to "
+                       "page-locked host memory each step; whole-run throughput, no L2 flush inside"}
 
     extra = {}
     if not args.no_batched:

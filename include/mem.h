@@ -162,6 +162,18 @@ mem_status mem_fuse_pointcloud(mem_map *m, int64_t n, const float *xyz, int32_t 
                                const mem_source *sources, const double T_map_sensor[16],
                                void *stream);
 
+/* Same as mem_fuse_pointcloud with HOST buffers: xyz and every source's
+ * `data` are host memory (page-locked, e.g. cudaHostAlloc, for the upload to
+ * run asynchronously; pageable memory works but the host waits for its copy).
+ * The library copies them into one of two device staging buffers it owns,
+ * used in turn, on a copy stream of its own; the kernels wait for that copy
+ * on `stream`. The host buffers must stay unchanged until the call's work on
+ * `stream` has completed. Consecutive calls overlap one call's upload with
+ * the previous call's kernels. Errors as mem_fuse_pointcloud. */
+mem_status mem_fuse_pointcloud_host(mem_map *m, int64_t n, const float *xyz, int32_t n_sources,
+                                    const mem_source *sources, const double T_map_sensor[16],
+                                    void *stream);
+
 /* Fuse n_maps independent clouds into the n_maps maps of one object in one
  * pass. offsets: host int64 [n_maps + 1] CSR offsets into xyz and the
  * source rows; T_map_sensor: host float64 [n_maps][16]. Results equal

@@ -484,6 +484,12 @@ extern "C" mem_status mem_destroy_map(mem_map* mm) {
     if (m->h_job[s]) cudaFreeHost(m->h_job[s]);
     if (m->job_ev[s]) cudaEventDestroy(m->job_ev[s]);
   }
+  for (int k = 0; k < 2; ++k) {
+    if (m->stage_buf[k]) cudaFree(m->stage_buf[k]);
+    if (m->stage_copied[k]) cudaEventDestroy(m->stage_copied[k]);
+    if (m->stage_done[k]) cudaEventDestroy(m->stage_done[k]);
+  }
+  if (m->copy_stream) cudaStreamDestroy(m->copy_stream);
   delete mm;
   return MEM_OK;
 }
@@ -738,6 +744,70 @@ extern "C" mem_status mem_fuse_pointcloud(mem_map* mm, int64_t n, const float* x
   mem_status s = check_sources(m, n_sources, sources, src, false);
   if (s != MEM_OK) return s;
   return run_points(m, 1, nullptr, n, xyz, src, n_sources, T_map_sensor, true, (cudaStream_t)stream);
+}
+
+// Host-buffer variant of mem_fuse_pointcloud: the call's inputs are copied
+// into one of two device staging buffers (used in turn) on the map's copy
+// stream; the kernels wait for that copy on the caller's stream, and the
+// next call's copy waits only for the kernels that last read the same
+// buffer, so uploads overlap the previous call's fuse.
+extern "C" mem_status mem_fuse_pointcloud_host(mem_map* mm, int64_t n, const float* xyz, int32_t n_sources,
+                                               const mem_source* sources, const double T_map_sensor[16],
+                                               void* stream) {
+  if (!mm || !T_map_sensor) return fail(MEM_ERR_ARG, "NULL argument");
+  Map* m = &mm->m;
+  if (m->cfg.n_maps != 1) return fail(MEM_ERR_ARG, "map object holds %d maps: use mem_fuse_pointcloud_batch", m->cfg.n_maps);
+  if (n < 0 || n >= (1ll << 30)) return fail(MEM_ERR_ARG, "n out of range [0, 2^30)");
+  if (n > 0 && !xyz) return fail(MEM_ERR_ARG, "xyz is NULL");
+  if (!finite16(T_map_sensor)) return fail(MEM_ERR_ARG, "pose not finite");
+  SrcDev src[MEM_MAX_SOURCES];
+  mem_status s = check_sources(m, n_sources, sources, src, false);
+  if (s != MEM_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  // layout of the staging buffer: xyz, then every source's rows, 256-byte aligned
+  size_t off[MEM_MAX_SOURCES + 1], bytes = 0;
+  auto take = [&](size_t b) {
+    const size_t o = bytes;
+    bytes += (b + 255) & ~(size_t)255;
+    return o;
+  };
+  off[0] = take((size_t)n * 12);
+  for (int q = 0; q < n_sources; ++q) off[q + 1] = take((size_t)n * src[q].C * dtype_size(src[q].dtype));
+  if (!m->copy_stream) {
+    CK(cudaStreamCreateWithFlags(&m->copy_stream, cudaStreamNonBlocking), "copy stream");
+    for (int k = 0; k < 2; ++k) {
+      CK(cudaEventCreateWithFlags(&m->stage_copied[k], cudaEventDisableTiming), "staging event");
+      CK(cudaEventCreateWithFlags(&m->stage_done[k], cudaEventDisableTiming), "staging event");
+    }
+  }
+  const int k = m->stage_slot;
+  m->stage_slot ^= 1;
+  if (bytes > m->stage_cap[k]) {  // grow (waits for every use of the old buffer)
+    CK(cudaEventSynchronize(m->stage_done[k]), "staging sync");
+    if (m->stage_buf[k]) cudaFree(m->stage_buf[k]);
+    m->stage_buf[k] = nullptr;
+    m->stage_cap[k] = 0;
+    CK(cudaMalloc(&m->stage_buf[k], bytes + bytes / 4), "staging buffer");
+    m->stage_cap[k] = bytes + bytes / 4;
+  }
+  char* d = (char*)m->stage_buf[k];
+  CK(cudaStreamWaitEvent(m->copy_stream, m->stage_done[k], 0), "staging wait");
+  if (n > 0) {
+    CK(cudaMemcpyAsync(d + off[0], xyz, (size_t)n * 12, cudaMemcpyHostToDevice, m->copy_stream), "upload xyz");
+    for (int q = 0; q < n_sources; ++q) {
+      CK(cudaMemcpyAsync(d + off[q + 1], sources[q].data, (size_t)n * src[q].C * dtype_size(src[q].dtype),
+                         cudaMemcpyHostToDevice, m->copy_stream),
+         "upload source");
+      src[q].data = d + off[q + 1];
+      src[q].vec_ok = 1;  // 256-byte aligned
+    }
+  }
+  CK(cudaEventRecord(m->stage_copied[k], m->copy_stream), "staging record");
+  CK(cudaStreamWaitEvent(st, m->stage_copied[k], 0), "staging wait");
+  s = run_points(m, 1, nullptr, n, (const float*)(d + off[0]), src, n_sources, T_map_sensor, true, st);
+  if (s != MEM_OK) return s;
+  CK(cudaEventRecord(m->stage_done[k], st), "staging record");
+  return MEM_OK;
 }
 
 extern "C" mem_status mem_fuse_pointcloud_batch(mem_map* mm, const int64_t* offsets, const float* xyz,

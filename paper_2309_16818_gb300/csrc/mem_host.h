@@ -45,6 +45,14 @@ struct Map {
   std::vector<ProfMark> prof_pending;
   double prof_ms[16] = {};
   int64_t prof_calls[16] = {};
+  // host-buffer fuse: two device staging buffers used in turn, filled on a
+  // copy stream of the map's own so that a call's upload overlaps the
+  // previous call's kernels
+  void* stage_buf[2] = {};
+  size_t stage_cap[2] = {};
+  cudaEvent_t stage_copied[2] = {}, stage_done[2] = {};
+  cudaStream_t copy_stream = nullptr;
+  int stage_slot = 0;
   // allocations to free
   std::vector<void*> allocs;
   std::vector<void*> scratch_allocs;

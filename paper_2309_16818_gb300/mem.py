@@ -24,7 +24,7 @@ LAYER_HEIGHT, LAYER_VARIANCE, LAYER_VALID, LAYER_NACC, LAYER_NREJ = -1, -2, -3, 
 PART_VALUE, PART_THETA, PART_VAR, PART_OBSERVED = range(4)
 
 EXPORTS = ["mem_create_map", "mem_destroy_map", "mem_move_map", "mem_fuse_pointcloud",
-           "mem_fuse_pointcloud_batch", "mem_fuse_image", "mem_get_layer", "mem_set_layer",
+           "mem_fuse_pointcloud_host", "mem_fuse_pointcloud_batch", "mem_fuse_image", "mem_get_layer", "mem_set_layer",
            "mem_get_origin", "mem_check", "mem_last_error", "mem_set_tuning", "mem_get_tuning",
            "mem_set_profiling", "mem_get_profile", "mem_get_stats", "mem_fuse_pointcloud_noalloc",
            "mem_autotune_batch", "mem_inpaint_diffusion", "mem_unet_create", "mem_unet_destroy",
@@ -75,6 +75,7 @@ def lib():
             "mem_create_map": [P, P], "mem_destroy_map": [P],
             "mem_move_map": [P, I32, P, P],
             "mem_fuse_pointcloud": [P, I64, P, I32, P, P, P],
+            "mem_fuse_pointcloud_host": [P, I64, P, I32, P, P, P],
             "mem_fuse_pointcloud_batch": [P, P, P, I32, P, P, P],
             "mem_fuse_image": [P, I32, I32, I32, I32, P, P, P, P, P, P],
             "mem_get_layer": [P, I32, I32, I32, P, P], "mem_set_layer": [P, I32, I32, I32, P, P],
@@ -215,10 +216,10 @@ class Map:
             pass
 
     # -- inputs -------------------------------------------------------------------
-    def _sources(self, sources, keep):
+    def _sources(self, sources, keep, on_host=False):
         arr = (Source * MAX_SOURCES)()
         for i, (t, layers) in enumerate(sources):
-            assert t.is_cuda and t.is_contiguous()
+            assert t.is_cuda != on_host and t.is_contiguous()
             keep.append(t)
             arr[i].data = t.data_ptr()
             arr[i].dtype = _dtype_code(t)
@@ -236,6 +237,17 @@ class Map:
         n = int(xyz.shape[0])
         _ck(lib().mem_fuse_pointcloud(self._h, n, C.c_void_p(xyz.data_ptr() if n else 0),
                                       len(sources), src, _pose(T).ctypes.data, _stream(stream)))
+
+    def fuse_pointcloud_host(self, xyz, T, sources=(), stream=None):
+        """As fuse_pointcloud with CPU tensors (pinned for an asynchronous upload): the library
+        copies them to device staging buffers of its own, overlapping the previous call's
+        kernels. The tensors must stay unchanged until the call's work on `stream` is done."""
+        keep = []
+        src = self._sources(list(sources), keep, on_host=True)
+        assert not xyz.is_cuda and xyz.is_contiguous()
+        n = int(xyz.shape[0])
+        _ck(lib().mem_fuse_pointcloud_host(self._h, n, C.c_void_p(xyz.data_ptr() if n else 0),
+                                           len(sources), src, _pose(T).ctypes.data, _stream(stream)))
 
     def fuse_pointcloud_batch(self, offsets, xyz, T, sources=(), stream=None):
         keep = []

@@ -231,3 +231,34 @@ def test_run_to_run_identical_with_moves(torch):
         else:
             for j, (a, b) in enumerate(zip(ref, out)):
                 assert a == b, (trial, j)
+
+
+def test_host_buffer_fuse_equals_device_fuse(torch):
+    """mem_fuse_pointcloud_host (pinned host inputs, library staging buffers used in turn on a
+    copy stream) gives the same layers as the device-pointer call, pose after pose."""
+    from paper_2309_16818_gb300 import mem as M
+    c = synth.config2(n_poses=4, scale=0.5)
+    layers = [M.Layer(3, M.LATEST), M.Layer(20, M.DIRICHLET), M.Layer(20, M.CLASSMAX),
+              M.Layer(20, M.EXPAVG, w=0.1)]
+    dev = M.Map(c["W"], c["res"], layers, max_points=1 << 20)
+    host = M.Map(c["W"], c["res"], layers, max_points=1 << 20)
+    side = torch.cuda.Stream()
+    pinned = []
+    for k, s in enumerate(c["scans"]):
+        hx = torch.from_numpy(s.xyz).pin_memory()
+        hr = torch.from_numpy(s.rgb).pin_memory()
+        hp = torch.from_numpy(s.probs).pin_memory()
+        pinned.append((hx, hr, hp))  # alive until the stream is synchronized
+        dev.move(c["poses"][k][:2])
+        dev.fuse_pointcloud(hx.cuda(), s.T, [(hr.cuda(), [0]), (hp.cuda(), [1, 2, 3])])
+        with torch.cuda.stream(side):
+            host.move(c["poses"][k][:2])
+            host.fuse_pointcloud_host(hx, s.T, [(hr, [0]), (hp, [1, 2, 3])])
+    torch.cuda.synchronize()
+    side.synchronize()
+    dev.check()
+    host.check()
+    for lay in (M.LAYER_HEIGHT, M.LAYER_VARIANCE, M.LAYER_VALID, M.LAYER_NACC, M.LAYER_NREJ, 0, 1, 2, 3):
+        a = dev.get_layer(lay).cpu().numpy()
+        b = host.get_layer(lay).cpu().numpy()
+        assert np.array_equal(a.view(np.uint8), b.view(np.uint8)), lay
