@@ -235,9 +235,9 @@ mem_status mem_autotune_batch(mem_map *m, const int64_t *offsets, const float *x
 #define MEM_PROFILE_SLOTS 16
 mem_status mem_set_profiling(mem_map *m, int32_t on);
 mem_status mem_get_profile(mem_map *m, double ms[MEM_PROFILE_SLOTS], int64_t calls[MEM_PROFILE_SLOTS]);
-/* Synchronise `stream`; out = {cells whose points cross a 32-point window of
- * the sorted order, touched cells, kept points, radix passes} of the last
- * point fuse (host output). */
+/* Synchronise `stream`; out = {cells whose points cross a tile of 128
+ * sorted points, touched cells, kept points, radix passes} of the last point
+ * fuse (host output). */
 mem_status mem_get_stats(mem_map *m, void *stream, int64_t out[4]);
 
 /* Diffusion (harmonic) inpainting of a batch of map crops, the fallback of the
