@@ -230,8 +230,8 @@ void free_scratch(Map* m) {
 
 cudaError_t alloc_scratch(Map* m, int64_t cap) {
   MapDev& md = m->md;
-  cap = cap < 4096 ? 4096 : cap;
-  const int64_t tiles = (cap + 4095) / 4096;
+  cap = cap < kSortTile ? kSortTile : cap;
+  const int64_t tiles = (cap + kSortTile - 1) / kSortTile;
   cudaError_t e;
   void* p;
 #define A(field, type, count)                                               \
@@ -661,8 +661,11 @@ static mem_status ensure_capacity(Map* m, int64_t n) {
 
 // Builds and uploads the job block, then queues the kernel sequence
 // (replayed from a CUDA graph when `graph` is set and the stream allows it).
+// The job block is uploaded on `job_st` (default: `st`); with `ready` set, the
+// kernels on `st` wait for an event recorded on `job_st` after that upload.
 static mem_status run_points(Map* m, int nm, const int64_t* offsets, int64_t n, const float* xyz,
-                             const SrcDev* src, int n_src, const double* T, bool graph, cudaStream_t st) {
+                             const SrcDev* src, int n_src, const double* T, bool graph, cudaStream_t st,
+                             cudaStream_t job_st = nullptr, cudaEvent_t ready = nullptr) {
   mem_status s = ensure_capacity(m, n);
   if (s != MEM_OK) return s;
   std::string buf(m->job_bytes, '\0');
@@ -701,8 +704,12 @@ static mem_status run_points(Map* m, int nm, const int64_t* offsets, int64_t n, 
     for (int b = 0; b <= nm; ++b) offs[b] = offsets[b];
     bytes += sizeof(int64_t) * (nm + 1);
   }
-  s = stage_job(m, h, bytes, st);
+  s = stage_job(m, h, bytes, ready ? job_st : st);
   if (s != MEM_OK) return s;
+  if (ready) {
+    CK(cudaEventRecord(ready, job_st), "job upload record");
+    CK(cudaStreamWaitEvent(st, ready, 0), "job upload wait");
+  }
   if (n == 0) return MEM_OK;
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   if (graph && st) cudaStreamIsCapturing(st, &cap);
@@ -802,9 +809,9 @@ extern "C" mem_status mem_fuse_pointcloud_host(mem_map* mm, int64_t n, const flo
       src[q].vec_ok = 1;  // 256-byte aligned
     }
   }
-  CK(cudaEventRecord(m->stage_copied[k], m->copy_stream), "staging record");
-  CK(cudaStreamWaitEvent(st, m->stage_copied[k], 0), "staging wait");
-  s = run_points(m, 1, nullptr, n, (const float*)(d + off[0]), src, n_sources, T_map_sensor, true, st);
+  // the job block follows the inputs on the copy stream; the kernels wait for both
+  s = run_points(m, 1, nullptr, n, (const float*)(d + off[0]), src, n_sources, T_map_sensor, true, st,
+                 m->copy_stream, m->stage_copied[k]);
   if (s != MEM_OK) return s;
   CK(cudaEventRecord(m->stage_done[k], st), "staging record");
   return MEM_OK;

@@ -19,7 +19,7 @@ namespace {
 using memk::u32;
 
 constexpr int64_t kMaxPts = MEM_NOALLOC_MAX_POINTS;
-constexpr int64_t kTiles = kMaxPts / 4096;
+constexpr int64_t kTiles = (kMaxPts + memk::kSortTile - 1) / memk::kSortTile;
 constexpr int64_t kAlign = 64;  // u32 words = 256 bytes
 constexpr int64_t up(int64_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 // word offsets of the sub-arrays

@@ -19,9 +19,7 @@
 
 namespace memk {
 
-constexpr int kSortThreads = 256;
-constexpr int kSortItems = 16;
-constexpr int kTile = kSortThreads * kSortItems;  // keys per radix tile
+constexpr int kTile = kSortTile;  // keys per radix tile
 constexpr u32 kLbA = 1u << 30;                    // aggregate published
 constexpr u32 kLbP = 2u << 30;                    // inclusive prefix published
 constexpr u32 kLbFlags = 3u << 30;
