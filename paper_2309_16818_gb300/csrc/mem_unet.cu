@@ -2,15 +2,15 @@
 // kernels (float32 accumulation, float32 master weights, Adam).
 //
 // Layout: activations NHWC bf16. A 3x3 convolution is an implicit GEMM
-// C[pixels, cout] = A[pixels, 9*cin] B[9*cin, cout]: every block stages a
-// 64-pixel x 32-channel slice of the (virtual) im2col matrix and a 32 x BN
-// slice of the weights in shared memory with cp.async (zero fill at the
-// border), and its four warps run m16n8k16 BF16 MMAs from ldmatrix
-// fragments. The decoder's nearest-neighbour upsampling and channel
-// concatenation are folded into that gather (two input tensors, the first at
-// half resolution). The data gradient is the same kernel with flipped,
-// transposed weights; the weight gradient is a GEMM over pixels split across
-// blocks with float32 atomics.
+// C[pixels, cout] = A[pixels, 9*cin] B[9*cin, cout]: every block stages the
+// input halo of an 8 x 16 output tile (32 channels at a time) and a 32 x BN
+// slice of the weights per tap in shared memory with cp.async (zero fill at
+// the border), and its eight warps run m16n8k16 BF16 MMAs from ldmatrix
+// fragments, all nine taps from one staged halo. The decoder's
+// nearest-neighbour upsampling and channel concatenation are folded into
+// that gather (two input tensors, the first at half resolution). The data
+// gradient is the same kernel with flipped, transposed weights; the weight
+// gradient is a GEMM over pixels split across blocks with float32 atomics.
 #include <math.h>
 #include <string.h>
 
@@ -55,7 +55,7 @@ __device__ __forceinline__ void mma_bf16(float d[4], const u32 a[4], u32 b0, u32
 }
 
 // ---------------------------------------------------------------------------
-// implicit-GEMM 3x3 convolution (forward, and data gradient)
+// 3x3 convolution (forward, and data gradient with flipped weights)
 
 struct ConvArgs {
   const bf16* in0;  // [N, H(/2), W(/2), c0]
@@ -68,97 +68,97 @@ struct ConvArgs {
   int cout, N, H, W, relu;
 };
 
-constexpr int kBM = 64, kBK = 32;
-constexpr int kApad = kBK + 8;  // smem row of A: 80 bytes (conflict-free ldmatrix)
+// ---------------------------------------------------------------------------
+// 3x3 convolution on halo tiles: a block computes an 8 x 16 tile of output
+// pixels for BN output channels. For every 32-channel chunk of the input it
+// stages the tile's (8 + 2) x (16 + 2) input halo once (zero outside the
+// image; nearest upsampling and channel concatenation folded into the
+// gather), then runs the nine taps from it, streaming the weights of one
+// (chunk, tap) at a time; halo and weights are double-buffered with
+// cp.async. Eight warps: 4 along pixels (32 each) x 2 along channels.
+
+constexpr int kTH = 8, kTW = 16;                  // output tile
+constexpr int kHH = kTH + 2, kHW = kTW + 2;       // halo tile
+constexpr int kHS = 40;                           // bf16 per halo pixel (32 + 8: conflict-free ldmatrix)
 
 template <int BN>
-__global__ void __launch_bounds__(128) k_conv3x3(ConvArgs a) {
+__global__ void __launch_bounds__(256) k_conv3x3h(ConvArgs a) {
   constexpr int kBpad = BN + 8;
-  __shared__ __align__(16) bf16 As[2][kBM][kApad];
-  __shared__ __align__(16) bf16 Bs[2][kBK][kBpad];
+  __shared__ __align__(16) bf16 Hs[2][kHH * kHW * kHS];
+  __shared__ __align__(16) bf16 Bs[2][32][kBpad];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int wm = warp >> 1, wn = warp & 1;  // 2 x 2 warps, warp tile 32 x BN/2
-  const int64_t M = (int64_t)a.N * a.H * a.W;
-  const int64_t m0 = (int64_t)blockIdx.x * kBM;
+  const int wm = warp >> 1, wn = warp & 1;
+  const int tx = (a.W + kTW - 1) / kTW, ty = (a.H + kTH - 1) / kTH;
+  int b = blockIdx.x;
+  const int n = b / (tx * ty);
+  b -= n * tx * ty;
+  const int y0 = (b / tx) * kTH, x0 = (b % tx) * kTW;
   const int n0 = blockIdx.y * BN;
-  const int HW = a.H * a.W;
-  // the two A rows this thread stages, and its 8-channel chunk
-  int rn[2], ry[2], rx[2];
-  bool rok[2];
-  const int ck = tid & 3;
-#pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    const int64_t p = m0 + (tid >> 2) + 32 * i;
-    rok[i] = p < M;
-    const int64_t pp = rok[i] ? p : 0;
-    rn[i] = (int)(pp / HW);
-    const int rem = (int)(pp - (int64_t)rn[i] * HW);
-    ry[i] = rem / a.W;
-    rx[i] = rem - ry[i] * a.W;
-  }
-  const int kchunks = a.cin_pad / kBK;
-  const int ksteps = 9 * kchunks;
-  auto stage = [&](int ks, int buf) {
-    const int t = ks / kchunks, cb = (ks - t * kchunks) * kBK;
-    const int dy = t / 3 - 1, dx = t % 3 - 1;
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-      const int r = (tid >> 2) + 32 * i;
-      const int yy = ry[i] + dy, xx = rx[i] + dx;
+  const int kchunks = a.cin_pad / 32;
+  const int S = kchunks * 9;
+  auto stage_halo = [&](int c, int buf) {
+    const int cb = c * 32;
+    for (int i = tid; i < kHH * kHW * 4; i += 256) {
+      const int hp = i >> 2, ck = i & 3;
+      const int hy = hp / kHW, hx = hp - hy * kHW;
+      const int yy = y0 + hy - 1, xx = x0 + hx - 1;
       const int ci = cb + 8 * ck;
-      bool ok = rok[i] && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W && ci < a.c0 + a.c1;
+      const bool ok = yy >= 0 && yy < a.H && xx >= 0 && xx < a.W && ci < a.c0 + a.c1;
       const bf16* src = a.in0;
       if (ok) {
         if (ci < a.c0) {
-          if (a.up0) {
-            const int Hh = a.H >> 1, Wh = a.W >> 1;
-            src = a.in0 + (((int64_t)rn[i] * Hh + (yy >> 1)) * Wh + (xx >> 1)) * a.c0 + ci;
-          } else {
-            src = a.in0 + (((int64_t)rn[i] * a.H + yy) * a.W + xx) * a.c0 + ci;
-          }
+          if (a.up0) src = a.in0 + (((int64_t)n * (a.H >> 1) + (yy >> 1)) * (a.W >> 1) + (xx >> 1)) * a.c0 + ci;
+          else src = a.in0 + (((int64_t)n * a.H + yy) * a.W + xx) * a.c0 + ci;
         } else {
-          src = a.in1 + (((int64_t)rn[i] * a.H + yy) * a.W + xx) * a.c1 + (ci - a.c0);
+          src = a.in1 + (((int64_t)n * a.H + yy) * a.W + xx) * a.c1 + (ci - a.c0);
         }
       }
-      cp_async16(&As[buf][r][8 * ck], src, ok);
+      cp_async16(&Hs[buf][hp * kHS + 8 * ck], src, ok);
     }
-    // weights: 32 rows x BN columns
-    constexpr int CPR = BN / 8;  // 16-byte chunks per row
-#pragma unroll
-    for (int i = 0; i < (kBK * CPR) / 128; ++i) {
-      const int c = tid + 128 * i;
-      const int r = c / CPR, cc = c - r * CPR;
-      const bf16* src = a.w + ((int64_t)(t * a.cin_pad + cb + r) * a.cout + n0 + 8 * cc);
-      cp_async16(&Bs[buf][r][8 * cc], src, true);
-    }
-    cp_async_commit();
   };
-  constexpr int NT = BN / 16;  // n8 tiles per warp
+  auto stage_w = [&](int c, int t, int buf) {
+    constexpr int CPR = BN / 8;
+    for (int i = tid; i < 32 * CPR; i += 256) {
+      const int r = i / CPR, cc = i - r * CPR;
+      cp_async16(&Bs[buf][r][8 * cc], a.w + ((int64_t)(t * a.cin_pad + c * 32 + r) * a.cout + n0 + 8 * cc), true);
+    }
+  };
+  constexpr int NT = BN / 16;
   float acc[2][NT][4];
 #pragma unroll
   for (int i = 0; i < 2; ++i)
 #pragma unroll
     for (int j = 0; j < NT; ++j) acc[i][j][0] = acc[i][j][1] = acc[i][j][2] = acc[i][j][3] = 0.f;
-  stage(0, 0);
-  for (int ks = 0; ks < ksteps; ++ks) {
-    const int buf = ks & 1;
-    if (ks + 1 < ksteps) {
-      stage(ks + 1, buf ^ 1);
+  stage_halo(0, 0);
+  stage_w(0, 0, 0);
+  cp_async_commit();
+  for (int st = 0; st < S; ++st) {
+    const int c = st / 9, t = st - c * 9;
+    if (st + 1 < S) {
+      const int c1 = (st + 1) / 9, t1 = st + 1 - c1 * 9;
+      stage_w(c1, t1, (st + 1) & 1);
+      if (t1 == 0) stage_halo(c1, c1 & 1);
+      cp_async_commit();
       cp_async_wait1();
     } else {
       cp_async_wait0();
     }
     __syncthreads();
+    const bf16* H = Hs[c & 1];
+    const int dy = t / 3, dx = t - dy * 3;  // halo offset of the tap
 #pragma unroll
-    for (int kk = 0; kk < kBK; kk += 16) {
+    for (int kk = 0; kk < 32; kk += 16) {
       u32 af[2][4];
 #pragma unroll
-      for (int mt = 0; mt < 2; ++mt)
-        ldsm_x4(af[mt], &As[buf][wm * 32 + mt * 16 + (lane & 15)][kk + (lane >> 4) * 8]);
+      for (int mt = 0; mt < 2; ++mt) {
+        const int pp = wm * 32 + mt * 16 + (lane & 15);  // output pixel of this ldmatrix row
+        const int hp = ((pp >> 4) + dy) * kHW + (pp & 15) + dx;
+        ldsm_x4(af[mt], &H[hp * kHS + kk + (lane >> 4) * 8]);
+      }
 #pragma unroll
       for (int np = 0; np < NT / 2; ++np) {
         u32 bfr[4];
-        ldsm_x4_t(bfr, &Bs[buf][kk + (lane & 7) + ((lane >> 3) & 1) * 8][wn * (BN / 2) + np * 16 + (lane >> 4) * 8]);
+        ldsm_x4_t(bfr, &Bs[st & 1][kk + (lane & 7) + ((lane >> 3) & 1) * 8][wn * (BN / 2) + np * 16 + (lane >> 4) * 8]);
 #pragma unroll
         for (int mt = 0; mt < 2; ++mt) {
           mma_bf16(acc[mt][2 * np], af[mt], bfr[0], bfr[1]);
@@ -172,12 +172,14 @@ __global__ void __launch_bounds__(128) k_conv3x3(ConvArgs a) {
 #pragma unroll
   for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-    for (int nt = 0; nt < NT; ++nt)
+    for (int h = 0; h < 2; ++h) {
+      const int pp = wm * 32 + mt * 16 + (lane >> 2) + 8 * h;
+      const int yy = y0 + (pp >> 4), xx = x0 + (pp & 15);
+      if (yy >= a.H || xx >= a.W) continue;
+      bf16* o = a.out + (((int64_t)n * a.H + yy) * a.W + xx) * a.cout;
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int64_t p = m0 + wm * 32 + mt * 16 + (lane >> 2) + 8 * h;
+      for (int nt = 0; nt < NT; ++nt) {
         const int co = n0 + wn * (BN / 2) + nt * 8 + (lane & 3) * 2;
-        if (p >= M) continue;
         float v0 = acc[mt][nt][2 * h], v1 = acc[mt][nt][2 * h + 1];
         if (a.bias) {
           v0 += a.bias[co];
@@ -187,8 +189,9 @@ __global__ void __launch_bounds__(128) k_conv3x3(ConvArgs a) {
           v0 = fmaxf(v0, 0.f);
           v1 = fmaxf(v1, 0.f);
         }
-        *reinterpret_cast<__nv_bfloat162*>(a.out + p * a.cout + co) = __floats2bfloat162_rn(v0, v1);
+        *reinterpret_cast<__nv_bfloat162*>(o + co) = __floats2bfloat162_rn(v0, v1);
       }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -597,15 +600,12 @@ cudaError_t conv(mem_unet* u, const ConvLayer& c, const bf16* in0, const bf16* i
   a.H = H;
   a.W = W;
   a.relu = relu;
-  const int64_t M = (int64_t)N * H * W;
   (void)c;
-  if (cout % 64 == 0) {
-    dim3 g((unsigned)((M + kBM - 1) / kBM), cout / 64);
-    k_conv3x3<64><<<g, 128, 0, st>>>(a);
-  } else {
-    dim3 g((unsigned)((M + kBM - 1) / kBM), cout / 32);
-    k_conv3x3<32><<<g, 128, 0, st>>>(a);
-  }
+  if (cout % 32 != 0 || cin_pad % 32 != 0) return cudaErrorInvalidValue;
+  const unsigned tiles = (unsigned)(N * ((H + kTH - 1) / kTH) * ((W + kTW - 1) / kTW));
+  if (cout % 128 == 0) k_conv3x3h<128><<<dim3(tiles, cout / 128), 256, 0, st>>>(a);
+  else if (cout % 64 == 0) k_conv3x3h<64><<<dim3(tiles, cout / 64), 256, 0, st>>>(a);
+  else k_conv3x3h<32><<<dim3(tiles, cout / 32), 256, 0, st>>>(a);
   return cudaGetLastError();
 }
 
