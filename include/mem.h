@@ -261,7 +261,8 @@ mem_status mem_inpaint_diffusion(int32_t n_crops, int32_t H, int32_t W, const fl
  * added to the diffusion fill. Four levels of widths[0..3] channels, two 3x3
  * convolutions + ReLU per level, 2x2 max-pooling, nearest upsampling with
  * skip concatenation [upsampled, skip], a final 1x1 convolution. BF16
- * tensor-core kernels with float32 accumulation; float32 master weights.
+ * tensor-core kernels (tcgen05, accumulator in tensor memory) with float32
+ * accumulation; float32 master weights.
  * Parameters (flat float32, in this order): for each 3x3 convolution
  * e1a e1b e2a e2b e3a e3b e4a e4b d3a d3b d2a d2b d1a d1b its weights
  * [3][3][C_in][C_out] then bias [C_out]; then the 1x1 weights [widths[0]] and
@@ -287,6 +288,10 @@ mem_status mem_unet_gradients(mem_unet *u, int32_t n, int32_t H, int32_t W, cons
 mem_status mem_unet_train_step(mem_unet *u, int32_t n, int32_t H, int32_t W, const float *x3,
                                const float *fill, const float *target, const uint8_t *hidden,
                                int64_t n_hidden, float lr, float *loss, void *stream);
+/* Synchronises the stream and reports a device-side failure of this net's
+ * kernels (a bounded wait inside a convolution that ran out) as
+ * MEM_ERR_TIMEOUT, clearing the error word; MEM_OK otherwise. */
+mem_status mem_unet_check(mem_unet *u, void *stream);
 
 /* Allocation-free height fuse. The paper has no counterpart: this entry point
  * exists for callers that cannot call cudaMalloc -- code that runs inside

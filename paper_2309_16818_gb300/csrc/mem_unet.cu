@@ -2,15 +2,17 @@
 // kernels (float32 accumulation, float32 master weights, Adam).
 //
 // Layout: activations NHWC bf16. A 3x3 convolution is an implicit GEMM
-// C[pixels, cout] = A[pixels, 9*cin] B[9*cin, cout]: every block stages the
-// input halo of an 8 x 16 output tile (32 channels at a time) and a 32 x BN
-// slice of the weights per tap in shared memory with cp.async (zero fill at
-// the border), and its eight warps run m16n8k16 BF16 MMAs from ldmatrix
-// fragments, all nine taps from one staged halo. The decoder's
-// nearest-neighbour upsampling and channel concatenation are folded into
-// that gather (two input tensors, the first at half resolution). The data
+// C[pixels, cout] = A[pixels, 9*cin] B[9*cin, cout] on the tcgen05 tensor
+// cores: a block gathers the input halo of a 16 x 16 output tile (16
+// channels per pipeline stage, cp.async, zero fill at the border) and the
+// stage's packed weights (one bulk copy) into shared memory, one thread issues
+// the MMAs of all nine taps from that one halo (descriptors offset per tap),
+// and the float32 accumulator lives in tensor memory until the epilogue. The
+// decoder's nearest-neighbour upsampling and channel concatenation are folded
+// into the gather (two input tensors, the first at half resolution). The data
 // gradient is the same kernel with flipped, transposed weights; the weight
-// gradient is a GEMM over pixels split across blocks with float32 atomics.
+// gradient is a GEMM over pixels split across blocks with float32 atomics
+// (warp-level mma.sync).
 #include <math.h>
 #include <string.h>
 
@@ -36,11 +38,6 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
 
-__device__ __forceinline__ void ldsm_x4(u32 r[4], const void* p) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(smem_u32(p)));
-}
 __device__ __forceinline__ void ldsm_x4_t(u32 r[4], const void* p) {
   asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
@@ -55,143 +52,320 @@ __device__ __forceinline__ void mma_bf16(float d[4], const u32 a[4], u32 b0, u32
 }
 
 // ---------------------------------------------------------------------------
+// 5th-generation tensor cores (tcgen05): shared-memory operands, TMEM
+// accumulator, mbarrier completion; bounded waits
+
+__device__ __forceinline__ void mbar_init(u32 bar, u32 count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(u32 bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(u32 bar, u32 bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+// wait for the phase of the given parity; false (and the error word set) after about 2^31 cycles
+__device__ __forceinline__ bool mbar_wait(u32 bar, u32 parity, int* err) {
+  const long long t0 = clock64();
+  for (;;) {
+    u32 ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > (1ll << 31)) {
+      atomicExch(err, 1);
+      return false;
+    }
+  }
+}
+// bulk copy global -> shared, completion counted in bytes on an mbarrier
+__device__ __forceinline__ void bulk_g2s(u32 dst, const void* src, u32 bytes, u32 bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async16s(u32 dst, const void* src, bool valid) {
+  const int n = valid ? 16 : 0;
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(n) : "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait_n() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// shared-memory matrix descriptor, no swizzle: K-major core matrices of 8 rows x 16 bytes, `lbo`
+// bytes apart along K and `sbo` bytes apart along M (or N); bit 46 is the descriptor version
+__device__ __forceinline__ uint64_t sdesc(u32 saddr, u32 lbo, u32 sbo) {
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+// D[tmem] (+)= A[smem] B[smem]^T, BF16 inputs, float32 accumulator
+__device__ __forceinline__ void mma_bf16_tc(u32 d_tmem, uint64_t ad, uint64_t bd, u32 idesc, u32 accumulate) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// arrive on the mbarrier once every MMA issued so far by this thread has completed
+__device__ __forceinline__ void mma_commit(u32 bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+// 16 consecutive float32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld16(u32 taddr, u32 v[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// ---------------------------------------------------------------------------
 // 3x3 convolution (forward, and data gradient with flipped weights)
 
 struct ConvArgs {
   const bf16* in0;  // [N, H(/2), W(/2), c0]
   const bf16* in1;  // [N, H, W, c1] or null
   int c0, c1, up0;  // up0: in0 is at half resolution (nearest upsample)
-  int cin_pad;      // rows of the weight matrix per tap (multiple of 32, >= c0 + c1)
-  const bf16* w;    // [9][cin_pad][cout]
+  int cin_pad;      // input channels of the packed weights (multiple of 16, >= c0 + c1)
+  const bf16* w;    // packed [cout / BN][cin_pad / 16][9 taps][2][BN][8] (see conv_bn)
   const float* bias;
   bf16* out;        // [N, H, W, cout]
   int cout, N, H, W, relu;
+  int* err;         // set when a bounded wait runs out
+  int store;        // write `out` (0: only the fused outputs below are wanted)
+  bf16* pool;       // optional 2x2 max pooling of the output, [N, H/2, W/2, cout]
+  // optional fused 1x1 head (one column block only): pred = fill + head_b + sum_c head_w[c] out[c]
+  const float* head_w;
+  const float* head_b;
+  const float* fill;
+  float* pred;
 };
 
-// ---------------------------------------------------------------------------
-// 3x3 convolution on halo tiles: a block computes an 8 x 16 tile of output
-// pixels for BN output channels. For every 32-channel chunk of the input it
-// stages the tile's (8 + 2) x (16 + 2) input halo once (zero outside the
-// image; nearest upsampling and channel concatenation folded into the
-// gather), then runs the nine taps from it, streaming the weights of one
-// (chunk, tap) at a time; halo and weights are double-buffered with
-// cp.async. Eight warps: 4 along pixels (32 each) x 2 along channels.
+// output channels per block: the largest of 128, 64, 32 that divides cout
+__host__ __device__ inline int conv_bn(int cout) { return cout % 128 == 0 ? 128 : (cout % 64 == 0 ? 64 : 32); }
 
-constexpr int kTH = 8, kTW = 16;                  // output tile
-constexpr int kHH = kTH + 2, kHW = kTW + 2;       // halo tile
-constexpr int kHS = 40;                           // bf16 per halo pixel (32 + 8: conflict-free ldmatrix)
+// A block computes a 16 x 16 tile of output pixels for BN output channels as
+// an implicit GEMM on the tensor cores: D[256 pixels, BN] accumulates in TMEM
+// as two M = 128 halves (16 rows x 8 columns of pixels each), K = 9 taps x
+// the input channels. The input is consumed 16 channels per pipeline stage:
+// the 18 x 18 halo of the tile is gathered into shared memory as two planes
+// of 8 channels (16 bytes per pixel, zero outside the image; nearest
+// upsampling and channel concatenation folded into the gather), so the
+// 8-pixel rows of a tap's A operand are eight consecutive 16-byte halo
+// pixels: each tap is the same halo read through a descriptor offset by
+// (dy * 18 + dx) pixels, with 288 bytes between pixel rows and one plane
+// between the two 8-channel halves of K. The stage's weights (9 taps x 16
+// channels x BN, packed host-side in core-matrix order) arrive with one bulk
+// copy. Warp 0 allocates TMEM and one thread issues the 18 MMAs of a stage;
+// warps 1..7 gather halos and keep up to NST stages in flight; completion
+// runs on mbarriers (stage full: 224 gather arrivals + the weight bytes;
+// stage empty: MMA commit). All eight warps then read the accumulator back
+// (warp w: TMEM lanes 32 (w % 4).., half w / 4), add bias, apply ReLU and
+// store bf16.
+constexpr int kTY = 16, kTX = 16;              // output tile
+constexpr int kHY = kTY + 2, kHX = kTX + 2;    // input halo
+constexpr int kHaloBytes = 2 * kHY * kHX * 16;  // 16 channels as two 8-channel planes
+constexpr int kConvProd = 224;                 // gathering threads (warps 1..7)
 
-template <int BN>
-__global__ void __launch_bounds__(256) k_conv3x3h(ConvArgs a) {
-  constexpr int kBpad = BN + 8;
-  __shared__ __align__(16) bf16 Hs[2][kHH * kHW * kHS];
-  __shared__ __align__(16) bf16 Bs[2][32][kBpad];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int wm = warp >> 1, wn = warp & 1;
-  const int tx = (a.W + kTW - 1) / kTW, ty = (a.H + kTH - 1) / kTH;
+template <int BN, int NST>
+struct ConvCfg {
+  static constexpr int kWBytes = 9 * 2 * BN * 16;      // weights of one stage
+  static constexpr int kSlot = kHaloBytes + kWBytes;   // one pipeline slot
+  static constexpr int kSmem = NST * kSlot + 128;      // + barriers and the TMEM address
+  static constexpr int kCols = 2 * BN;                 // TMEM columns (two halves)
+  static constexpr int kLag = NST - 2 > 0 ? NST - 2 : 1;  // copy groups a gatherer keeps open
+};
+
+template <int BN, int NST>
+__global__ void __launch_bounds__(256, BN == 32 ? 4 : 1) k_conv3x3t(ConvArgs a) {
+  using C = ConvCfg<BN, NST>;
+  constexpr int kLag = C::kLag;
+  extern __shared__ __align__(1024) unsigned char sm[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  unsigned char* tail = sm + NST * C::kSlot;
+  u32* tmem_slot = reinterpret_cast<u32*>(tail + 8 * (2 * NST + 1));
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  const u32 sbase = smem_u32(sm), bar0 = smem_u32(tail);  // full[s] at bar0 + 8 s, empty[s] after them
+  const u32 done_bar = bar0 + 8 * (2 * NST);
+  const int tx = (a.W + kTX - 1) / kTX, ty = (a.H + kTY - 1) / kTY;
   int b = blockIdx.x;
   const int n = b / (tx * ty);
   b -= n * tx * ty;
-  const int y0 = (b / tx) * kTH, x0 = (b % tx) * kTW;
-  const int n0 = blockIdx.y * BN;
-  const int kchunks = a.cin_pad / 32;
-  const int S = kchunks * 9;
-  auto stage_halo = [&](int c, int buf) {
-    const int cb = c * 32;
-    for (int i = tid; i < kHH * kHW * 4; i += 256) {
-      const int hp = i >> 2, ck = i & 3;
-      const int hy = hp / kHW, hx = hp - hy * kHW;
-      const int yy = y0 + hy - 1, xx = x0 + hx - 1;
-      const int ci = cb + 8 * ck;
-      const bool ok = yy >= 0 && yy < a.H && xx >= 0 && xx < a.W && ci < a.c0 + a.c1;
-      const bf16* src = a.in0;
-      if (ok) {
-        if (ci < a.c0) {
-          if (a.up0) src = a.in0 + (((int64_t)n * (a.H >> 1) + (yy >> 1)) * (a.W >> 1) + (xx >> 1)) * a.c0 + ci;
-          else src = a.in0 + (((int64_t)n * a.H + yy) * a.W + xx) * a.c0 + ci;
-        } else {
-          src = a.in1 + (((int64_t)n * a.H + yy) * a.W + xx) * a.c1 + (ci - a.c0);
-        }
-      }
-      cp_async16(&Hs[buf][hp * kHS + 8 * ck], src, ok);
+  const int y0 = (b / tx) * kTY, x0 = (b % tx) * kTX;
+  const int nb = blockIdx.y;
+  const int cin = a.c0 + a.c1;
+  const int S = (cin + 15) / 16, CS = a.cin_pad / 16;  // stages past the real channels are all zero
+  if (tid == 0) {
+    for (int s = 0; s < NST; ++s) {
+      mbar_init(bar0 + 8 * s, kConvProd + 1);
+      mbar_init(bar0 + 8 * (NST + s), 1);
     }
-  };
-  auto stage_w = [&](int c, int t, int buf) {
-    constexpr int CPR = BN / 8;
-    for (int i = tid; i < 32 * CPR; i += 256) {
-      const int r = i / CPR, cc = i - r * CPR;
-      cp_async16(&Bs[buf][r][8 * cc], a.w + ((int64_t)(t * a.cin_pad + c * 32 + r) * a.cout + n0 + 8 * cc), true);
-    }
-  };
-  constexpr int NT = BN / 16;
-  float acc[2][NT][4];
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < NT; ++j) acc[i][j][0] = acc[i][j][1] = acc[i][j][2] = acc[i][j][3] = 0.f;
-  stage_halo(0, 0);
-  stage_w(0, 0, 0);
-  cp_async_commit();
-  for (int st = 0; st < S; ++st) {
-    const int c = st / 9, t = st - c * 9;
-    if (st + 1 < S) {
-      const int c1 = (st + 1) / 9, t1 = st + 1 - c1 * 9;
-      stage_w(c1, t1, (st + 1) & 1);
-      if (t1 == 0) stage_halo(c1, c1 & 1);
-      cp_async_commit();
-      cp_async_wait1();
-    } else {
-      cp_async_wait0();
-    }
-    __syncthreads();
-    const bf16* H = Hs[c & 1];
-    const int dy = t / 3, dx = t - dy * 3;  // halo offset of the tap
-#pragma unroll
-    for (int kk = 0; kk < 32; kk += 16) {
-      u32 af[2][4];
-#pragma unroll
-      for (int mt = 0; mt < 2; ++mt) {
-        const int pp = wm * 32 + mt * 16 + (lane & 15);  // output pixel of this ldmatrix row
-        const int hp = ((pp >> 4) + dy) * kHW + (pp & 15) + dx;
-        ldsm_x4(af[mt], &H[hp * kHS + kk + (lane >> 4) * 8]);
-      }
-#pragma unroll
-      for (int np = 0; np < NT / 2; ++np) {
-        u32 bfr[4];
-        ldsm_x4_t(bfr, &Bs[st & 1][kk + (lane & 7) + ((lane >> 3) & 1) * 8][wn * (BN / 2) + np * 16 + (lane >> 4) * 8]);
-#pragma unroll
-        for (int mt = 0; mt < 2; ++mt) {
-          mma_bf16(acc[mt][2 * np], af[mt], bfr[0], bfr[1]);
-          mma_bf16(acc[mt][2 * np + 1], af[mt], bfr[2], bfr[3]);
-        }
-      }
-    }
-    __syncthreads();
+    mbar_init(done_bar, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  // epilogue: bias, ReLU, bf16 pairs
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(C::kCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const u32 tmem = *tmem_slot;
+  if (warp == 0) {
+    if (lane == 0) {
+      // instruction descriptor: f32 accumulator, bf16 A and B, both K-major, N = BN, M = 128
+      const u32 idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((u32)(BN >> 3) << 17) | ((u32)(128 >> 4) << 24);
+      for (int s = 0; s < S; ++s) {
+        const int slot = s % NST;
+        if (!mbar_wait(bar0 + 8 * slot, (s / NST) & 1, a.err)) {
+          *abort_flag = 1;
+          break;
+        }
+        tc_fence_after();
+        const u32 hb = sbase + slot * C::kSlot, wb = hb + kHaloBytes;
 #pragma unroll
-  for (int mt = 0; mt < 2; ++mt)
+        for (int t = 0; t < 9; ++t) {
+          const int dy = t / 3, dx = t % 3;
+          const uint64_t bd = sdesc(wb + t * 2 * BN * 16, BN * 16, 128);
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int pp = wm * 32 + mt * 16 + (lane >> 2) + 8 * h;
-      const int yy = y0 + (pp >> 4), xx = x0 + (pp & 15);
-      if (yy >= a.H || xx >= a.W) continue;
-      bf16* o = a.out + (((int64_t)n * a.H + yy) * a.W + xx) * a.cout;
+          for (int h = 0; h < 2; ++h) {
+            const uint64_t ad = sdesc(hb + (dy * kHX + 8 * h + dx) * 16, kHY * kHX * 16, kHX * 16);
+            mma_bf16_tc(tmem + h * BN, ad, bd, idesc, (s | t) != 0);
+          }
+        }
+        mma_commit(bar0 + 8 * (NST + slot));
+      }
+      mma_commit(done_bar);
+    }
+  } else {
+    const int pt = tid - 32;
+    int s = 0;
+    for (; s < S; ++s) {
+      const int slot = s % NST;
+      if (s >= NST && !mbar_wait(bar0 + 8 * (NST + slot), ((s / NST) - 1) & 1, a.err)) {
+        *abort_flag = 1;
+        break;
+      }
+      if (*abort_flag) break;
+      const u32 hb = sbase + slot * C::kSlot;
+      if (pt == 0) {
+        mbar_arrive_tx(bar0 + 8 * slot, C::kWBytes);
+        bulk_g2s(hb + kHaloBytes, a.w + (int64_t)(nb * CS + s) * (9 * 2 * BN * 8), C::kWBytes, bar0 + 8 * slot);
+      }
+      for (int i = pt; i < 2 * kHY * kHX; i += kConvProd) {
+        const int hp = i >> 1, g = i & 1;
+        const int hy = hp / kHX, hx = hp - hy * kHX;
+        const int yy = y0 + hy - 1, xx = x0 + hx - 1;
+        const int ci = s * 16 + 8 * g;
+        const bool ok = yy >= 0 && yy < a.H && xx >= 0 && xx < a.W && ci < cin;
+        const bf16* src = a.in0;
+        if (ok) {
+          if (ci < a.c0) {
+            if (a.up0) src = a.in0 + (((int64_t)n * (a.H >> 1) + (yy >> 1)) * (a.W >> 1) + (xx >> 1)) * a.c0 + ci;
+            else src = a.in0 + (((int64_t)n * a.H + yy) * a.W + xx) * a.c0 + ci;
+          } else {
+            src = a.in1 + (((int64_t)n * a.H + yy) * a.W + xx) * a.c1 + (ci - a.c0);
+          }
+        }
+        cp_async16s(hb + (g * kHY * kHX + hp) * 16, src, ok);
+      }
+      cp_async_commit();
+      if (s >= kLag) {  // the group of stage s - kLag is complete: publish it to the tensor core
+        cp_async_wait_n<kLag>();
+        fence_proxy_async();
+        mbar_arrive(bar0 + 8 * ((s - kLag) % NST));
+      }
+    }
+    cp_async_wait0();
+    fence_proxy_async();
+    for (int r = s - kLag < 0 ? 0 : s - kLag; r < s; ++r) mbar_arrive(bar0 + 8 * (r % NST));
+  }
+  bool ok = mbar_wait(done_bar, 0, a.err);
+  tc_fence_after();
+  ok = __all_sync(0xffffffffu, ok && !*abort_flag);
+  if (ok) {
+    const int h = warp >> 2, q = warp & 3;
+    const int m = q * 32 + lane;  // accumulator row = pixel (m / 8, 8 h + m % 8) of the tile
+    const int yy = y0 + (m >> 3), xx = x0 + 8 * h + (m & 7);
+    const bool inside = yy < a.H && xx < a.W;
+    const int64_t pix = ((int64_t)n * a.H + (inside ? yy : 0)) * a.W + (inside ? xx : 0);
+    bf16* o = a.out + pix * a.cout + nb * BN;
+    // pooling partners: lanes ^1 (x + 1) and ^8 (y + 1); lane bits 0 and 3 clear = top-left pixel,
+    // and H, W are even wherever pooling happens, so a 2x2 window is wholly inside or outside
+    const bool pool_writer = inside && (lane & 9) == 0;
+    bf16* po = a.pool ? a.pool + (((int64_t)n * (a.H >> 1) + (yy >> 1)) * (a.W >> 1) + (xx >> 1)) * a.cout + nb * BN
+                      : nullptr;
+    float hr = a.head_w ? a.head_b[0] : 0.f;
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+      u32 v[16];
+      tmem_ld16(tmem + ((u32)(q * 32) << 16) + (u32)(h * BN + c0), v);
+      u32 pk[8];
 #pragma unroll
-      for (int nt = 0; nt < NT; ++nt) {
-        const int co = n0 + wn * (BN / 2) + nt * 8 + (lane & 3) * 2;
-        float v0 = acc[mt][nt][2 * h], v1 = acc[mt][nt][2 * h + 1];
+      for (int j = 0; j < 8; ++j) {
+        float f0 = __uint_as_float(v[2 * j]), f1 = __uint_as_float(v[2 * j + 1]);
         if (a.bias) {
-          v0 += a.bias[co];
-          v1 += a.bias[co + 1];
+          f0 += a.bias[nb * BN + c0 + 2 * j];
+          f1 += a.bias[nb * BN + c0 + 2 * j + 1];
         }
         if (a.relu) {
-          v0 = fmaxf(v0, 0.f);
-          v1 = fmaxf(v1, 0.f);
+          f0 = fmaxf(f0, 0.f);
+          f1 = fmaxf(f1, 0.f);
         }
-        *reinterpret_cast<__nv_bfloat162*>(o + co) = __floats2bfloat162_rn(v0, v1);
+        __nv_bfloat162 p2 = __floats2bfloat162_rn(f0, f1);
+        pk[j] = *reinterpret_cast<u32*>(&p2);
+      }
+      if (inside && a.store) {
+        uint4* dst = reinterpret_cast<uint4*>(o + c0);
+        dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+      }
+      if (po) {
+        u32 mx[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const u32 o1 = __shfl_xor_sync(0xffffffffu, pk[j], 1);
+          const u32 o8 = __shfl_xor_sync(0xffffffffu, pk[j], 8);
+          const u32 o9 = __shfl_xor_sync(0xffffffffu, pk[j], 9);
+          const float2 a0 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&pk[j]));
+          const float2 a1 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&o1));
+          const float2 a8 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&o8));
+          const float2 a9 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&o9));
+          __nv_bfloat162 r2 = __floats2bfloat162_rn(fmaxf(fmaxf(a0.x, a1.x), fmaxf(a8.x, a9.x)),
+                                                    fmaxf(fmaxf(a0.y, a1.y), fmaxf(a8.y, a9.y)));
+          mx[j] = *reinterpret_cast<u32*>(&r2);
+        }
+        if (pool_writer) {
+          uint4* dst = reinterpret_cast<uint4*>(po + c0);
+          dst[0] = make_uint4(mx[0], mx[1], mx[2], mx[3]);
+          dst[1] = make_uint4(mx[4], mx[5], mx[6], mx[7]);
+        }
+      }
+      if (a.head_w) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&pk[j]));
+          hr = fmaf(f.x, a.head_w[c0 + 2 * j], hr);
+          hr = fmaf(f.y, a.head_w[c0 + 2 * j + 1], hr);
+        }
       }
     }
+    if (a.head_w && inside) a.pred[pix] = a.fill[pix] + hr;
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::kCols) : "memory");
 }
 
 // ---------------------------------------------------------------------------
@@ -307,24 +481,6 @@ __global__ void __launch_bounds__(128) k_wgrad3x3(WgradArgs a) {
 
 // ---------------------------------------------------------------------------
 // element-wise pieces
-
-// 2x2 max pooling (NHWC)
-__global__ void k_maxpool(const bf16* __restrict__ x, bf16* __restrict__ y, int N, int H, int W, int C) {
-  const int Ho = H / 2, Wo = W / 2;
-  const int64_t total = (int64_t)N * Ho * Wo * C;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const int c = (int)(i % C);
-    int64_t r = i / C;
-    const int xo = (int)(r % Wo);
-    r /= Wo;
-    const int yo = (int)(r % Ho);
-    const int n = (int)(r / Ho);
-    const bf16* p = x + (((int64_t)n * H + 2 * yo) * W + 2 * xo) * C + c;
-    const float a = __bfloat162float(p[0]), b = __bfloat162float(p[C]);
-    const float d = __bfloat162float(p[(int64_t)W * C]), e = __bfloat162float(p[(int64_t)W * C + C]);
-    y[i] = __float2bfloat16_rn(fmaxf(fmaxf(a, b), fmaxf(d, e)));
-  }
-}
 
 // gradient of 2x2 max pooling to the first maximum of each window (row-major),
 // added to `acc` (the gradient that reached the same tensor through the skip)
@@ -445,25 +601,42 @@ __global__ void k_head(const bf16* __restrict__ d1, int C, const float* __restri
   }
 }
 
-// float32 master weights [3][3][cin][cout] -> bf16 forward copy [9][cin_pad][cout]
-// and (optionally) the data-gradient copy [9][cout_pad][cin] with flipped taps
+// index of weight (tap t, input channel ci, output channel co) in the packed
+// layout the convolution streams: [co / BN][ci / 16][t][(ci / 8) % 2][co % BN][ci % 8]
+// (one pipeline stage = one contiguous run of 9 x 16 x BN values)
+__device__ __forceinline__ void unpack_index(int64_t i, int BN, int CS, int& t, int& ci, int& co) {
+  const int k = (int)(i & 7);
+  int64_t r = i >> 3;
+  const int col = (int)(r % BN);
+  r /= BN;
+  const int g = (int)(r & 1);
+  r >>= 1;
+  t = (int)(r % 9);
+  r /= 9;
+  const int cs = (int)(r % CS), nb = (int)(r / CS);
+  ci = cs * 16 + g * 8 + k;
+  co = nb * BN + col;
+}
+
+// float32 master weights [3][3][cin][cout] -> packed bf16 forward weights (cin_pad
+// input channels) and (optionally) the data-gradient weights: taps flipped, roles of
+// input and output channels exchanged (cout_pad input channels, cin_out outputs)
 __global__ void k_prep_weights(const float* __restrict__ w, int cin, int cout, int cin_pad, bf16* __restrict__ wf,
                                bf16* __restrict__ wd, int cout_pad, int cin_out) {
   const int64_t nf = 9LL * cin_pad * cout;
+  const int bnf = conv_bn(cout), csf = cin_pad / 16;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nf; i += (int64_t)gridDim.x * blockDim.x) {
-    const int co = (int)(i % cout);
-    const int64_t r = i / cout;
-    const int ci = (int)(r % cin_pad), t = (int)(r / cin_pad);
+    int t, ci, co;
+    unpack_index(i, bnf, csf, t, ci, co);
     wf[i] = __float2bfloat16_rn(ci < cin ? w[((int64_t)t * cin + ci) * cout + co] : 0.f);
   }
   if (!wd) return;
   const int64_t nd = 9LL * cout_pad * cin_out;
+  const int bnd = conv_bn(cin_out), csd = cout_pad / 16;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nd; i += (int64_t)gridDim.x * blockDim.x) {
-    const int ci = (int)(i % cin_out);
-    const int64_t r = i / cin_out;
-    const int co = (int)(r % cout_pad), t = (int)(r / cout_pad);
-    const int tf = 8 - t;
-    wd[i] = __float2bfloat16_rn((co < cout && ci < cin) ? w[((int64_t)tf * cin + ci) * cout + co] : 0.f);
+    int t, k, j;  // k: input channel of the data-gradient conv (= layer output), j: its output (= layer input)
+    unpack_index(i, bnd, csd, t, k, j);
+    wd[i] = __float2bfloat16_rn((k < cout && j < cin) ? w[((int64_t)(8 - t) * cin + j) * cout + k] : 0.f);
   }
 }
 
@@ -535,6 +708,7 @@ struct mem_unet {
   bf16* dpool[3] = {};    // gradient of the pooled tensors
   float* d_loss = nullptr;
   float* g0pad = nullptr;  // weight gradient of the first layer with padded input channels
+  int* d_err = nullptr;    // set by a convolution whose bounded wait ran out
   int n_sm = 148;
 };
 
@@ -582,9 +756,30 @@ int grid_for(int64_t n, int n_sm) {
   return (int)(b < 1 ? 1 : (b > cap ? cap : b));
 }
 
+template <int BN, int NST>
+void launch_conv(dim3 grid, const ConvArgs& a, cudaStream_t st) {
+  using C = ConvCfg<BN, NST>;
+  static bool attr = false;  // dynamic shared memory above 48 KB is opted into once
+  if (!attr) {
+    cudaFuncSetAttribute(k_conv3x3t<BN, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
+    attr = true;
+  }
+  k_conv3x3t<BN, NST><<<grid, 256, C::kSmem, st>>>(a);
+}
+
+// outputs fused into a convolution's epilogue
+struct ConvFuse {
+  bool store = true;           // write the convolution output itself
+  bf16* pool = nullptr;        // 2x2 max pooling of the output
+  const float* head_w = nullptr;  // 1x1 head: pred = fill + head_b + head_w . out
+  const float* head_b = nullptr;
+  const float* fill = nullptr;
+  float* pred = nullptr;
+};
+
 cudaError_t conv(mem_unet* u, const ConvLayer& c, const bf16* in0, const bf16* in1, const bf16* w,
                  const float* bias, bf16* out, int cout, int cin_pad, int c0, int c1, int up0, int N, int H,
-                 int W, int relu, cudaStream_t st) {
+                 int W, int relu, cudaStream_t st, const ConvFuse& fz = ConvFuse()) {
   ConvArgs a;
   a.in0 = in0;
   a.in1 = in1;
@@ -600,12 +795,29 @@ cudaError_t conv(mem_unet* u, const ConvLayer& c, const bf16* in0, const bf16* i
   a.H = H;
   a.W = W;
   a.relu = relu;
+  a.err = u->d_err;
+  a.store = fz.store ? 1 : 0;
+  a.pool = fz.pool;
+  a.head_w = fz.head_w;
+  a.head_b = fz.head_b;
+  a.fill = fz.fill;
+  a.pred = fz.pred;
   (void)c;
-  if (cout % 32 != 0 || cin_pad % 32 != 0) return cudaErrorInvalidValue;
-  const unsigned tiles = (unsigned)(N * ((H + kTH - 1) / kTH) * ((W + kTW - 1) / kTW));
-  if (cout % 128 == 0) k_conv3x3h<128><<<dim3(tiles, cout / 128), 256, 0, st>>>(a);
-  else if (cout % 64 == 0) k_conv3x3h<64><<<dim3(tiles, cout / 64), 256, 0, st>>>(a);
-  else k_conv3x3h<32><<<dim3(tiles, cout / 32), 256, 0, st>>>(a);
+  if (cout % 32 != 0 || cin_pad % 16 != 0 || c0 % 8 != 0 || c1 % 8 != 0 || c0 + c1 > cin_pad)
+    return cudaErrorInvalidValue;
+  if ((fz.pool && (H % 2 || W % 2)) || (fz.head_w && conv_bn(cout) != cout)) return cudaErrorInvalidValue;
+  const dim3 grid((unsigned)(N * ((H + kTY - 1) / kTY) * ((W + kTX - 1) / kTX)), (unsigned)(cout / conv_bn(cout)));
+  // pipeline depth per column-block width (measured): 4 slots for 128 channels, 3 for 64, and
+  // for 32 channels 2 when the input has at most 32 channels (more blocks per SM), else 3
+  const int stages = (c0 + c1 + 15) / 16;
+  switch (conv_bn(cout)) {
+    case 128: launch_conv<128, 4>(grid, a, st); break;
+    case 64: launch_conv<64, 3>(grid, a, st); break;
+    default:
+      if (stages <= 2) launch_conv<32, 2>(grid, a, st);
+      else launch_conv<32, 3>(grid, a, st);
+      break;
+  }
   return cudaGetLastError();
 }
 
@@ -673,20 +885,31 @@ cudaError_t prep_weights(mem_unet* u, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t forward(mem_unet* u, int N, int H, int W, cudaStream_t st) {
+// The encoder levels' pooling runs in the epilogue of their second convolution.
+// With `pred` (inference), the 1x1 head runs in the epilogue of the last
+// convolution when that convolution is a single column block (widths[0] of 32,
+// 64 or 128), and its output is not stored; *head_done says whether it did.
+cudaError_t forward(mem_unet* u, int N, int H, int W, cudaStream_t st, const float* fill = nullptr,
+                    float* pred = nullptr, bool* head_done = nullptr) {
   cudaError_t e = cudaSuccess;
+  if (head_done) *head_done = false;
   for (size_t i = 0; i < u->L.size() && e == cudaSuccess; ++i) {
     const ConvLayer& c = u->L[i];
     const int l = c.level;
     const int Hl = H >> l, Wl = W >> l;
     const int c0 = i == 0 ? 16 : c.c0;
-    e = conv(u, c, input0(u, (int)i), input1(u, (int)i), c.wf, u->params + c.b_off, u->act[i], c.cout, c.cin_pad,
-             c0, c.c1, c.up0, N, Hl, Wl, 1, st);
-    if (i == 1 || i == 3 || i == 5) {  // pool the end of encoder levels 1..3
-      const int lv = (int)i / 2;
-      k_maxpool<<<grid_for((int64_t)N * (Hl / 2) * (Wl / 2) * c.cout, u->n_sm), 256, 0, st>>>(
-          u->act[i], u->pool[lv], N, Hl, Wl, c.cout);
+    ConvFuse fz;
+    if (i == 1 || i == 3 || i == 5) fz.pool = u->pool[i / 2];  // the end of encoder levels 1..3
+    if (i == 13 && pred && conv_bn(c.cout) == c.cout) {
+      fz.store = false;
+      fz.head_w = u->params + u->head_w;
+      fz.head_b = u->params + u->head_b;
+      fz.fill = fill;
+      fz.pred = pred;
+      if (head_done) *head_done = true;
     }
+    e = conv(u, c, input0(u, (int)i), input1(u, (int)i), c.wf, u->params + c.b_off, u->act[i], c.cout, c.cin_pad,
+             c0, c.c1, c.up0, N, Hl, Wl, 1, st, fz);
   }
   return e == cudaSuccess ? cudaGetLastError() : e;
 }
@@ -793,8 +1016,10 @@ extern "C" mem_status mem_unet_create(int32_t cin, const int32_t widths[4], mem_
   };
   if (cudaMalloc(&u->params, off * 4) != cudaSuccess || cudaMalloc(&u->grads, off * 4) != cudaSuccess ||
       cudaMalloc(&u->adam_m, off * 4) != cudaSuccess || cudaMalloc(&u->adam_v, off * 4) != cudaSuccess ||
-      cudaMalloc(&u->g0pad, 9ull * u->L[0].cin_pad * u->L[0].cout * 4) != cudaSuccess)
+      cudaMalloc(&u->g0pad, 9ull * u->L[0].cin_pad * u->L[0].cout * 4) != cudaSuccess ||
+      cudaMalloc(&u->d_err, sizeof(int)) != cudaSuccess)
     return fail_oom();
+  cudaMemset(u->d_err, 0, sizeof(int));
   cudaMemset(u->params, 0, off * 4);
   cudaMemset(u->adam_m, 0, off * 4);
   cudaMemset(u->adam_v, 0, off * 4);
@@ -820,6 +1045,7 @@ extern "C" mem_status mem_unet_destroy(mem_unet* u) {
   cudaFree(u->adam_m);
   cudaFree(u->adam_v);
   cudaFree(u->g0pad);
+  cudaFree(u->d_err);
   delete u;
   return MEM_OK;
 }
@@ -846,6 +1072,20 @@ extern "C" mem_status mem_unet_get_params(const mem_unet* u, float* dst, void* s
   return MEM_OK;
 }
 
+extern "C" mem_status mem_unet_check(mem_unet* u, void* stream) {
+  if (!u) return memh::api_fail(MEM_ERR_ARG, "NULL argument");
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return memh::api_cuda_fail(e, "stream synchronize");
+  int err = 0;
+  e = cudaMemcpy(&err, u->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return memh::api_cuda_fail(e, "read error word");
+  if (err) {
+    cudaMemset(u->d_err, 0, sizeof(int));
+    return memh::api_fail(MEM_ERR_TIMEOUT, "a bounded wait in a U-Net convolution ran out");
+  }
+  return MEM_OK;
+}
+
 static mem_status check_shape(const mem_unet* u, int32_t n, int32_t H, int32_t W) {
   if (!u) return memh::api_fail(MEM_ERR_ARG, "NULL net");
   if (n < 1 || H < 8 || W < 8 || H % 8 || W % 8) return memh::api_fail(MEM_ERR_ARG, "H, W multiples of 8, n >= 1");
@@ -864,11 +1104,13 @@ extern "C" mem_status mem_unet_forward(mem_unet* u, int32_t n, int32_t H, int32_
   if (e != cudaSuccess) return memh::api_cuda_fail(e, "U-Net activations");
   const int64_t P = (int64_t)n * H * W;
   k_pack_input<<<grid_for(P * 16, u->n_sm), 256, 0, st>>>(x3, u->x16, P);
-  e = forward(u, n, H, W, st);
+  bool head_done = false;
+  e = forward(u, n, H, W, st, fill, pred, &head_done);
   if (e != cudaSuccess) return memh::api_cuda_fail(e, "U-Net forward");
-  k_head<<<grid_for(P, u->n_sm), 256, 0, st>>>(u->act[13], u->widths[0], u->params + u->head_w,
-                                                u->params + u->head_b, fill, pred, nullptr, nullptr, 0.f, P,
-                                                nullptr, nullptr, nullptr, nullptr);
+  if (!head_done)
+    k_head<<<grid_for(P, u->n_sm), 256, 0, st>>>(u->act[13], u->widths[0], u->params + u->head_w,
+                                                  u->params + u->head_b, fill, pred, nullptr, nullptr, 0.f, P,
+                                                  nullptr, nullptr, nullptr, nullptr);
   e = cudaGetLastError();
   if (e != cudaSuccess) return memh::api_cuda_fail(e, "U-Net head");
   return MEM_OK;

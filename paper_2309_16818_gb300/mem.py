@@ -29,7 +29,7 @@ EXPORTS = ["mem_create_map", "mem_destroy_map", "mem_move_map", "mem_fuse_pointc
            "mem_set_profiling", "mem_get_profile", "mem_get_stats", "mem_fuse_pointcloud_noalloc",
            "mem_autotune_batch", "mem_inpaint_diffusion", "mem_unet_create", "mem_unet_destroy",
            "mem_unet_param_count", "mem_unet_set_params", "mem_unet_get_params", "mem_unet_forward",
-           "mem_unet_gradients", "mem_unet_train_step"]
+           "mem_unet_gradients", "mem_unet_train_step", "mem_unet_check"]
 NOALLOC_MAX_POINTS = 1 << 18
 PROFILE_SLOTS = ["key", "digit_scan", "radix_sort", "unused3", "fuse_tiles", "fuse_cross",
                  "time_var", "image", "move"]
@@ -90,6 +90,7 @@ def lib():
             "mem_unet_forward": [P, I32, I32, I32, P, P, P, P],
             "mem_unet_gradients": [P, I32, I32, I32, P, P, P, P, I64, P, P, P],
             "mem_unet_train_step": [P, I32, I32, I32, P, P, P, P, I64, C.c_float, P, P],
+            "mem_unet_check": [P, P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -418,3 +419,7 @@ class UNet:
         _ck(lib().mem_unet_train_step(self._h, n, H, W, _ptr(x3), _ptr(fill), _ptr(target), _ptr(hidden), nh,
                                       lr, _ptr(loss), _stream(stream)))
         return loss
+
+    def check(self, stream=None):
+        """Synchronise and raise MemError if a bounded device wait ran out."""
+        _ck(lib().mem_unet_check(self._h, _stream(stream)))
