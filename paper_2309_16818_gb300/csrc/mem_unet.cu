@@ -13,6 +13,8 @@
 // gradient is the same kernel with flipped, transposed weights; the weight
 // gradient is a GEMM over pixels split across blocks with float32 atomics
 // (warp-level mma.sync).
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <math.h>
 #include <string.h>
 
@@ -87,6 +89,15 @@ __device__ __forceinline__ void bulk_g2s(u32 dst, const void* src, u32 bytes, u3
                "l"(src), "r"(bytes), "r"(bar)
                : "memory");
 }
+// tiled TMA load of a 4-D box (coordinates innermost first) into shared memory; elements
+// outside the tensor read as zero
+__device__ __forceinline__ void tma_load_4d(u32 dst, const CUtensorMap* map, int c, int x, int y, int n, u32 bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c), "r"(x), "r"(y), "r"(n), "r"(bar)
+      : "memory");
+}
 __device__ __forceinline__ void cp_async16s(u32 dst, const void* src, bool valid) {
   const int n = valid ? 16 : 0;
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(n) : "memory");
@@ -151,61 +162,78 @@ struct ConvArgs {
 // output channels per block: the largest of 128, 64, 32 that divides cout
 __host__ __device__ inline int conv_bn(int cout) { return cout % 128 == 0 ? 128 : (cout % 64 == 0 ? 64 : 32); }
 
-// A block computes a 16 x 16 tile of output pixels for BN output channels as
-// an implicit GEMM on the tensor cores: D[256 pixels, BN] accumulates in TMEM
-// as two M = 128 halves (16 rows x 8 columns of pixels each), K = 9 taps x
-// the input channels. The input is consumed 16 channels per pipeline stage:
-// the 18 x 18 halo of the tile is gathered into shared memory as two planes
-// of 8 channels (16 bytes per pixel, zero outside the image; nearest
-// upsampling and channel concatenation folded into the gather), so the
-// 8-pixel rows of a tap's A operand are eight consecutive 16-byte halo
-// pixels: each tap is the same halo read through a descriptor offset by
-// (dy * 18 + dx) pixels, with 288 bytes between pixel rows and one plane
-// between the two 8-channel halves of K. The stage's weights (9 taps x 16
-// channels x BN, packed host-side in core-matrix order) arrive with one bulk
-// copy. Warp 0 allocates TMEM and one thread issues the 18 MMAs of a stage;
-// warps 1..7 gather halos and keep up to NST stages in flight; completion
-// runs on mbarriers (stage full: 224 gather arrivals + the weight bytes;
-// stage empty: MMA commit). All eight warps then read the accumulator back
-// (warp w: TMEM lanes 32 (w % 4).., half w / 4), add bias, apply ReLU and
-// store bf16.
+// A work item is a 16 x 16 tile of output pixels for BN output channels,
+// computed as an implicit GEMM on the tensor cores: D[256 pixels, BN]
+// accumulates in TMEM as two M = 128 halves (16 rows x 8 columns of pixels
+// each), K = 9 taps x the input channels. The input is consumed 16 channels
+// per pipeline stage: the 18 x 18 halo of the tile arrives in shared memory
+// as two planes of 8 channels (16 bytes per pixel) by two TMA box loads,
+// which read zero outside the image, so the 8-pixel rows of a tap's A operand
+// are eight consecutive 16-byte halo pixels: every tap reads the same halo
+// through a descriptor offset by (dy * 18 + dx) pixels, with 288 bytes between
+// pixel rows and one plane between the two 8-channel halves of K. The
+// decoder's concatenation is a choice of tensor map per stage; its nearest
+// upsampling loads the 10 x 10 half-resolution box and the gather warps
+// replicate it into the halo planes. The stage's weights (9 taps x 16
+// channels x BN, packed in core-matrix order) arrive with one bulk copy.
+//
+// The kernel is persistent (a block loops over work items) and warp
+// specialised: warp 0 owns TMEM and one of its threads issues the 18 MMAs of
+// each stage; warps 1..3 fill an NST-slot ring that runs across work items
+// (one thread issues the copies); warps 4..7 drain the accumulator (warp w
+// reads TMEM lanes 32 (w % 4)..), add bias, apply ReLU, store bf16 and the
+// fused outputs. The accumulator is double-buffered in TMEM, so one item's
+// epilogue overlaps the next item's MMAs. mbarriers: slot full (96 gather
+// arrivals + the copied bytes), slot empty (MMA commit), half-resolution
+// staging full (its bytes), accumulator full (MMA commit), accumulator empty
+// (128 epilogue arrivals). Every wait is bounded.
 constexpr int kTY = 16, kTX = 16;              // output tile
 constexpr int kHY = kTY + 2, kHX = kTX + 2;    // input halo
-constexpr int kHaloBytes = 2 * kHY * kHX * 16;  // 16 channels as two 8-channel planes
-constexpr int kConvProd = 224;                 // gathering threads (warps 1..7)
+constexpr int kPlaneBytes = kHY * kHX * 16;    // one 8-channel halo plane as loaded (5184)
+constexpr int kPlane = 5248;                   // its stride in shared memory (128-byte multiple)
+constexpr int kHalfBox = 10;                   // half-resolution box side for upsampled input
+constexpr int kStgBytes = kHalfBox * kHalfBox * 16;  // one plane of it (1600)
+constexpr int kStg = 1664;                     // its stride in shared memory
+constexpr int kConvProd = 96;                  // gathering threads (warps 1..3)
+constexpr int kConvEpi = 128;                  // epilogue threads (warps 4..7)
 
 template <int BN, int NST>
 struct ConvCfg {
-  static constexpr int kWBytes = 9 * 2 * BN * 16;      // weights of one stage
-  static constexpr int kSlot = kHaloBytes + kWBytes;   // one pipeline slot
-  static constexpr int kSmem = NST * kSlot + 128;      // + barriers and the TMEM address
-  static constexpr int kCols = 2 * BN;                 // TMEM columns (two halves)
-  static constexpr int kLag = NST - 2 > 0 ? NST - 2 : 1;  // copy groups a gatherer keeps open
+  static constexpr int kWBytes = 9 * 2 * BN * 16;             // weights of one stage
+  static constexpr int kSlot = 2 * kPlane + kWBytes + 2 * kStg;  // one pipeline slot
+  static constexpr int kSmem = NST * kSlot + 256 + 1024;      // + barriers, alignment slack
+  static constexpr int kCols = 4 * BN;                        // TMEM columns: 2 buffers x 2 halves
+  static constexpr int kMaxBlocksPerSm = 512 / kCols;         // TMEM holds 512 columns
 };
 
 template <int BN, int NST>
-__global__ void __launch_bounds__(256, BN == 32 ? 4 : 1) k_conv3x3t(ConvArgs a) {
+__global__ void __launch_bounds__(256, ConvCfg<BN, NST>::kMaxBlocksPerSm)
+    k_conv3x3t(const __grid_constant__ CUtensorMap tm0, const __grid_constant__ CUtensorMap tm1, ConvArgs a) {
   using C = ConvCfg<BN, NST>;
-  constexpr int kLag = C::kLag;
-  extern __shared__ __align__(1024) unsigned char sm[];
+  extern __shared__ __align__(1024) unsigned char sm_raw[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const u32 sbase = (smem_u32(sm_raw) + 1023u) & ~1023u;  // slots start 1024-byte aligned
+  unsigned char* sm = sm_raw + (sbase - smem_u32(sm_raw));
+  // barriers: full[NST], empty[NST], stage[NST], acc_full[2], acc_empty[2], done; TMEM address; abort
   unsigned char* tail = sm + NST * C::kSlot;
-  u32* tmem_slot = reinterpret_cast<u32*>(tail + 8 * (2 * NST + 1));
+  const u32 bar0 = sbase + NST * C::kSlot;
+  const u32 full0 = bar0, empty0 = bar0 + 8 * NST, stg0 = bar0 + 16 * NST, accf0 = bar0 + 24 * NST;
+  const u32 acce0 = accf0 + 16, done_bar = acce0 + 16;
+  u32* tmem_slot = reinterpret_cast<u32*>(tail + 24 * NST + 40);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  const u32 sbase = smem_u32(sm), bar0 = smem_u32(tail);  // full[s] at bar0 + 8 s, empty[s] after them
-  const u32 done_bar = bar0 + 8 * (2 * NST);
   const int tx = (a.W + kTX - 1) / kTX, ty = (a.H + kTY - 1) / kTY;
-  int b = blockIdx.x;
-  const int n = b / (tx * ty);
-  b -= n * tx * ty;
-  const int y0 = (b / tx) * kTY, x0 = (b % tx) * kTX;
-  const int nb = blockIdx.y;
-  const int cin = a.c0 + a.c1;
-  const int S = (cin + 15) / 16, CS = a.cin_pad / 16;  // stages past the real channels are all zero
+  const int NB = a.cout / BN;
+  const int items = a.N * tx * ty * NB;
+  const int S = (a.c0 + a.c1 + 15) / 16, CS = a.cin_pad / 16;  // stages past the real channels are all zero
   if (tid == 0) {
     for (int s = 0; s < NST; ++s) {
-      mbar_init(bar0 + 8 * s, kConvProd + 1);
-      mbar_init(bar0 + 8 * (NST + s), 1);
+      mbar_init(full0 + 8 * s, kConvProd + 1);
+      mbar_init(empty0 + 8 * s, 1);
+      mbar_init(stg0 + 8 * s, 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(accf0 + 8 * i, 1);
+      mbar_init(acce0 + 8 * i, kConvEpi);
     }
     mbar_init(done_bar, 1);
     *abort_flag = 0;
@@ -225,147 +253,196 @@ __global__ void __launch_bounds__(256, BN == 32 ? 4 : 1) k_conv3x3t(ConvArgs a) 
     if (lane == 0) {
       // instruction descriptor: f32 accumulator, bf16 A and B, both K-major, N = BN, M = 128
       const u32 idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((u32)(BN >> 3) << 17) | ((u32)(128 >> 4) << 24);
-      for (int s = 0; s < S; ++s) {
-        const int slot = s % NST;
-        if (!mbar_wait(bar0 + 8 * slot, (s / NST) & 1, a.err)) {
-          *abort_flag = 1;
+      int g = 0;  // stage counter across work items
+      bool run = true;
+      for (int w = blockIdx.x, it = 0; w < items && run; w += gridDim.x, ++it) {
+        const int ab = it & 1;
+        if (it >= 2 && !mbar_wait(acce0 + 8 * ab, ((it >> 1) - 1) & 1, a.err)) {
+          run = false;
           break;
         }
         tc_fence_after();
-        const u32 hb = sbase + slot * C::kSlot, wb = hb + kHaloBytes;
-#pragma unroll
-        for (int t = 0; t < 9; ++t) {
-          const int dy = t / 3, dx = t % 3;
-          const uint64_t bd = sdesc(wb + t * 2 * BN * 16, BN * 16, 128);
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const uint64_t ad = sdesc(hb + (dy * kHX + 8 * h + dx) * 16, kHY * kHX * 16, kHX * 16);
-            mma_bf16_tc(tmem + h * BN, ad, bd, idesc, (s | t) != 0);
+        const u32 acc = tmem + (u32)(ab * 2 * BN);
+        for (int s = 0; s < S; ++s, ++g) {
+          const int slot = g % NST;
+          if (!mbar_wait(full0 + 8 * slot, (g / NST) & 1, a.err)) {
+            run = false;
+            break;
           }
+          tc_fence_after();
+          const u32 hb = sbase + slot * C::kSlot, wb = hb + 2 * kPlane;
+#pragma unroll
+          for (int t = 0; t < 9; ++t) {
+            const int dy = t / 3, dx = t % 3;
+            const uint64_t bd = sdesc(wb + t * 2 * BN * 16, BN * 16, 128);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const uint64_t ad = sdesc(hb + (dy * kHX + 8 * h + dx) * 16, kPlane, kHX * 16);
+              mma_bf16_tc(acc + h * BN, ad, bd, idesc, (s | t) != 0);
+            }
+          }
+          mma_commit(empty0 + 8 * slot);
         }
-        mma_commit(bar0 + 8 * (NST + slot));
+        if (run) mma_commit(accf0 + 8 * ab);
       }
+      if (!run) *abort_flag = 1;
       mma_commit(done_bar);
     }
-  } else {
+  } else if (warp < 4) {
     const int pt = tid - 32;
-    int s = 0;
-    for (; s < S; ++s) {
-      const int slot = s % NST;
-      if (s >= NST && !mbar_wait(bar0 + 8 * (NST + slot), ((s / NST) - 1) & 1, a.err)) {
+    int g = 0;
+    u32 stg_phase = 0;  // bit per slot: parity of the next half-resolution load into it
+    bool run = true;
+    for (int w = blockIdx.x; w < items && run; w += gridDim.x) {
+      const int nb = w % NB;
+      int b = w / NB;
+      const int n = b / (tx * ty);
+      b -= n * tx * ty;
+      const int y0 = (b / tx) * kTY, x0 = (b % tx) * kTX;
+      for (int s = 0; s < S; ++s, ++g) {
+        const int slot = g % NST;
+        if ((g >= NST && !mbar_wait(empty0 + 8 * slot, ((g / NST) - 1) & 1, a.err)) || *abort_flag) {
+          run = false;
+          break;
+        }
+        const u32 hb = sbase + slot * C::kSlot, wb = hb + 2 * kPlane, sb = wb + C::kWBytes;
+        const int cb = s * 16;
+        const bool from0 = cb < a.c0, up = from0 && a.up0;
+        const CUtensorMap* map = from0 ? &tm0 : &tm1;
+        const int c = from0 ? cb : cb - a.c0;
+        if (pt == 0) {
+          const u32 bytes = C::kWBytes + (up ? 0u : 2u * kPlaneBytes);
+          mbar_arrive_tx(full0 + 8 * slot, bytes);
+          bulk_g2s(wb, a.w + (int64_t)(nb * CS + s) * (9 * 2 * BN * 8), C::kWBytes, full0 + 8 * slot);
+          if (up) {
+            mbar_arrive_tx(stg0 + 8 * slot, 2u * kStgBytes);
+            tma_load_4d(sb, map, c, (x0 >> 1) - 1, (y0 >> 1) - 1, n, stg0 + 8 * slot);
+            tma_load_4d(sb + kStg, map, c + 8, (x0 >> 1) - 1, (y0 >> 1) - 1, n, stg0 + 8 * slot);
+          } else {
+            tma_load_4d(hb, map, c, x0 - 1, y0 - 1, n, full0 + 8 * slot);
+            tma_load_4d(hb + kPlane, map, c + 8, x0 - 1, y0 - 1, n, full0 + 8 * slot);
+          }
+        }
+        if (up) {
+          // nearest upsampling: halo pixel (hy, hx) is half-resolution box pixel ((hy + 1) / 2, (hx + 1) / 2)
+          if (!mbar_wait(stg0 + 8 * slot, (stg_phase >> slot) & 1, a.err)) {
+            *abort_flag = 1;
+            run = false;
+          }
+          stg_phase ^= 1u << slot;
+          if (run) {
+            for (int i = pt; i < 2 * kHY * kHX; i += kConvProd) {
+              const int pl = i >= kHY * kHX, hp = i - pl * kHY * kHX;
+              const int hy = hp / kHX, hx = hp - hy * kHX;
+              const uint4 v = *reinterpret_cast<const uint4*>(sm + (sb - sbase) + pl * kStg +
+                                                              (((hy + 1) >> 1) * kHalfBox + ((hx + 1) >> 1)) * 16);
+              *reinterpret_cast<uint4*>(sm + (hb - sbase) + pl * kPlane + hp * 16) = v;
+            }
+            fence_proxy_async();
+          }
+        }
+        mbar_arrive(full0 + 8 * slot);
+        if (!run) break;
+      }
+    }
+  } else {
+    const int q = warp & 3;
+    const int m = q * 32 + lane;  // accumulator row = pixel (m / 8, 8 h + m % 8) of a tile half
+    for (int w = blockIdx.x, it = 0; w < items; w += gridDim.x, ++it) {
+      const int ab = it & 1;
+      bool ok = mbar_wait(accf0 + 8 * ab, (it >> 1) & 1, a.err);
+      ok = __all_sync(0xffffffffu, ok && !*abort_flag);
+      if (!ok) {
         *abort_flag = 1;
         break;
       }
-      if (*abort_flag) break;
-      const u32 hb = sbase + slot * C::kSlot;
-      if (pt == 0) {
-        mbar_arrive_tx(bar0 + 8 * slot, C::kWBytes);
-        bulk_g2s(hb + kHaloBytes, a.w + (int64_t)(nb * CS + s) * (9 * 2 * BN * 8), C::kWBytes, bar0 + 8 * slot);
-      }
-      for (int i = pt; i < 2 * kHY * kHX; i += kConvProd) {
-        const int hp = i >> 1, g = i & 1;
-        const int hy = hp / kHX, hx = hp - hy * kHX;
-        const int yy = y0 + hy - 1, xx = x0 + hx - 1;
-        const int ci = s * 16 + 8 * g;
-        const bool ok = yy >= 0 && yy < a.H && xx >= 0 && xx < a.W && ci < cin;
-        const bf16* src = a.in0;
-        if (ok) {
-          if (ci < a.c0) {
-            if (a.up0) src = a.in0 + (((int64_t)n * (a.H >> 1) + (yy >> 1)) * (a.W >> 1) + (xx >> 1)) * a.c0 + ci;
-            else src = a.in0 + (((int64_t)n * a.H + yy) * a.W + xx) * a.c0 + ci;
-          } else {
-            src = a.in1 + (((int64_t)n * a.H + yy) * a.W + xx) * a.c1 + (ci - a.c0);
+      tc_fence_after();
+      const int nb = w % NB;
+      int b = w / NB;
+      const int n = b / (tx * ty);
+      b -= n * tx * ty;
+      const int y0 = (b / tx) * kTY, x0 = (b % tx) * kTX;
+#pragma unroll 1
+      for (int h = 0; h < 2; ++h) {
+        const int yy = y0 + (m >> 3), xx = x0 + 8 * h + (m & 7);
+        const bool inside = yy < a.H && xx < a.W;
+        const int64_t pix = ((int64_t)n * a.H + (inside ? yy : 0)) * a.W + (inside ? xx : 0);
+        bf16* o = a.out + pix * a.cout + nb * BN;
+        // pooling partners: lanes ^1 (x + 1) and ^8 (y + 1); lane bits 0 and 3 clear = top-left
+        // pixel, and H, W are even wherever pooling happens, so a window is wholly inside or outside
+        const bool pool_writer = inside && (lane & 9) == 0;
+        bf16* po = a.pool ? a.pool + (((int64_t)n * (a.H >> 1) + (yy >> 1)) * (a.W >> 1) + (xx >> 1)) * a.cout +
+                                nb * BN
+                          : nullptr;
+        float hr = a.head_w ? a.head_b[0] : 0.f;
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+          u32 v[16];
+          tmem_ld16(tmem + ((u32)(q * 32) << 16) + (u32)(ab * 2 * BN + h * BN + c0), v);
+          u32 pk[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            float f0 = __uint_as_float(v[2 * j]), f1 = __uint_as_float(v[2 * j + 1]);
+            if (a.bias) {
+              f0 += a.bias[nb * BN + c0 + 2 * j];
+              f1 += a.bias[nb * BN + c0 + 2 * j + 1];
+            }
+            if (a.relu) {
+              f0 = fmaxf(f0, 0.f);
+              f1 = fmaxf(f1, 0.f);
+            }
+            __nv_bfloat162 p2 = __floats2bfloat162_rn(f0, f1);
+            pk[j] = *reinterpret_cast<u32*>(&p2);
+          }
+          if (inside && a.store) {
+            uint4* dst = reinterpret_cast<uint4*>(o + c0);
+            dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+          }
+          if (po) {
+            u32 mx[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const u32 o1 = __shfl_xor_sync(0xffffffffu, pk[j], 1);
+              const u32 o8 = __shfl_xor_sync(0xffffffffu, pk[j], 8);
+              const u32 o9 = __shfl_xor_sync(0xffffffffu, pk[j], 9);
+              const float2 a0 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&pk[j]));
+              const float2 a1 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&o1));
+              const float2 a8 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&o8));
+              const float2 a9 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&o9));
+              __nv_bfloat162 r2 = __floats2bfloat162_rn(fmaxf(fmaxf(a0.x, a1.x), fmaxf(a8.x, a9.x)),
+                                                        fmaxf(fmaxf(a0.y, a1.y), fmaxf(a8.y, a9.y)));
+              mx[j] = *reinterpret_cast<u32*>(&r2);
+            }
+            if (pool_writer) {
+              uint4* dst = reinterpret_cast<uint4*>(po + c0);
+              dst[0] = make_uint4(mx[0], mx[1], mx[2], mx[3]);
+              dst[1] = make_uint4(mx[4], mx[5], mx[6], mx[7]);
+            }
+          }
+          if (a.head_w) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&pk[j]));
+              hr = fmaf(f.x, a.head_w[c0 + 2 * j], hr);
+              hr = fmaf(f.y, a.head_w[c0 + 2 * j + 1], hr);
+            }
           }
         }
-        cp_async16s(hb + (g * kHY * kHX + hp) * 16, src, ok);
+        if (a.head_w && inside) a.pred[pix] = a.fill[pix] + hr;
       }
-      cp_async_commit();
-      if (s >= kLag) {  // the group of stage s - kLag is complete: publish it to the tensor core
-        cp_async_wait_n<kLag>();
-        fence_proxy_async();
-        mbar_arrive(bar0 + 8 * ((s - kLag) % NST));
-      }
+      tc_fence_before();
+      mbar_arrive(acce0 + 8 * ab);
     }
-    cp_async_wait0();
-    fence_proxy_async();
-    for (int r = s - kLag < 0 ? 0 : s - kLag; r < s; ++r) mbar_arrive(bar0 + 8 * (r % NST));
   }
-  bool ok = mbar_wait(done_bar, 0, a.err);
-  tc_fence_after();
-  ok = __all_sync(0xffffffffu, ok && !*abort_flag);
-  if (ok) {
-    const int h = warp >> 2, q = warp & 3;
-    const int m = q * 32 + lane;  // accumulator row = pixel (m / 8, 8 h + m % 8) of the tile
-    const int yy = y0 + (m >> 3), xx = x0 + 8 * h + (m & 7);
-    const bool inside = yy < a.H && xx < a.W;
-    const int64_t pix = ((int64_t)n * a.H + (inside ? yy : 0)) * a.W + (inside ? xx : 0);
-    bf16* o = a.out + pix * a.cout + nb * BN;
-    // pooling partners: lanes ^1 (x + 1) and ^8 (y + 1); lane bits 0 and 3 clear = top-left pixel,
-    // and H, W are even wherever pooling happens, so a 2x2 window is wholly inside or outside
-    const bool pool_writer = inside && (lane & 9) == 0;
-    bf16* po = a.pool ? a.pool + (((int64_t)n * (a.H >> 1) + (yy >> 1)) * (a.W >> 1) + (xx >> 1)) * a.cout + nb * BN
-                      : nullptr;
-    float hr = a.head_w ? a.head_b[0] : 0.f;
-#pragma unroll 1
-    for (int c0 = 0; c0 < BN; c0 += 16) {
-      u32 v[16];
-      tmem_ld16(tmem + ((u32)(q * 32) << 16) + (u32)(h * BN + c0), v);
-      u32 pk[8];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        float f0 = __uint_as_float(v[2 * j]), f1 = __uint_as_float(v[2 * j + 1]);
-        if (a.bias) {
-          f0 += a.bias[nb * BN + c0 + 2 * j];
-          f1 += a.bias[nb * BN + c0 + 2 * j + 1];
-        }
-        if (a.relu) {
-          f0 = fmaxf(f0, 0.f);
-          f1 = fmaxf(f1, 0.f);
-        }
-        __nv_bfloat162 p2 = __floats2bfloat162_rn(f0, f1);
-        pk[j] = *reinterpret_cast<u32*>(&p2);
-      }
-      if (inside && a.store) {
-        uint4* dst = reinterpret_cast<uint4*>(o + c0);
-        dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-        dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
-      }
-      if (po) {
-        u32 mx[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const u32 o1 = __shfl_xor_sync(0xffffffffu, pk[j], 1);
-          const u32 o8 = __shfl_xor_sync(0xffffffffu, pk[j], 8);
-          const u32 o9 = __shfl_xor_sync(0xffffffffu, pk[j], 9);
-          const float2 a0 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&pk[j]));
-          const float2 a1 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&o1));
-          const float2 a8 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&o8));
-          const float2 a9 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&o9));
-          __nv_bfloat162 r2 = __floats2bfloat162_rn(fmaxf(fmaxf(a0.x, a1.x), fmaxf(a8.x, a9.x)),
-                                                    fmaxf(fmaxf(a0.y, a1.y), fmaxf(a8.y, a9.y)));
-          mx[j] = *reinterpret_cast<u32*>(&r2);
-        }
-        if (pool_writer) {
-          uint4* dst = reinterpret_cast<uint4*>(po + c0);
-          dst[0] = make_uint4(mx[0], mx[1], mx[2], mx[3]);
-          dst[1] = make_uint4(mx[4], mx[5], mx[6], mx[7]);
-        }
-      }
-      if (a.head_w) {
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&pk[j]));
-          hr = fmaf(f.x, a.head_w[c0 + 2 * j], hr);
-          hr = fmaf(f.y, a.head_w[c0 + 2 * j + 1], hr);
-        }
-      }
-    }
-    if (a.head_w && inside) a.pred[pix] = a.fill[pix] + hr;
-  }
+  // every MMA this block issued has completed before its TMEM is released
+  mbar_wait(done_bar, 0, a.err);
   tc_fence_before();
   __syncthreads();
-  if (warp == 0)
+  if (warp == 0) {
+    tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::kCols) : "memory");
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -757,14 +834,48 @@ int grid_for(int64_t n, int n_sm) {
 }
 
 template <int BN, int NST>
-void launch_conv(dim3 grid, const ConvArgs& a, cudaStream_t st) {
+void launch_conv(int items, const CUtensorMap& tm0, const CUtensorMap& tm1, const ConvArgs& a, int n_sm,
+                 cudaStream_t st) {
   using C = ConvCfg<BN, NST>;
-  static bool attr = false;  // dynamic shared memory above 48 KB is opted into once
-  if (!attr) {
+  static int per_sm = 0;  // resident blocks per SM: shared memory per SM, capped by TMEM; set up once
+  if (!per_sm) {
     cudaFuncSetAttribute(k_conv3x3t<BN, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
-    attr = true;
+    int dev = 0, smem_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    const int by_smem = smem_sm / (C::kSmem + 1024);  // 1 KB per block is reserved by the system
+    per_sm = by_smem < 1 ? 1 : (by_smem > C::kMaxBlocksPerSm ? C::kMaxBlocksPerSm : by_smem);
   }
-  k_conv3x3t<BN, NST><<<grid, 256, C::kSmem, st>>>(a);
+  const int grid = items < n_sm * per_sm ? items : n_sm * per_sm;
+  k_conv3x3t<BN, NST><<<grid, 256, C::kSmem, st>>>(tm0, tm1, a);
+}
+
+// the driver's tensor-map encoder, looked up once through the runtime
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// NHWC bf16 activations [n][h][w][c] as a 4-D tensor (c innermost) read in boxes of
+// 8 channels x box x box pixels; false if the encoder is unavailable or refuses
+bool activation_map(CUtensorMap* m, const bf16* base, int c, int w, int h, int n, int box) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[4] = {(cuuint64_t)c, (cuuint64_t)w, (cuuint64_t)h, (cuuint64_t)n};
+  const cuuint64_t strides[3] = {(cuuint64_t)c * 2, (cuuint64_t)c * 2 * w, (cuuint64_t)c * 2 * w * h};
+  const cuuint32_t boxd[4] = {8, (cuuint32_t)box, (cuuint32_t)box, 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(base), dims, strides, boxd, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 // outputs fused into a convolution's epilogue
@@ -803,20 +914,29 @@ cudaError_t conv(mem_unet* u, const ConvLayer& c, const bf16* in0, const bf16* i
   a.fill = fz.fill;
   a.pred = fz.pred;
   (void)c;
-  if (cout % 32 != 0 || cin_pad % 16 != 0 || c0 % 8 != 0 || c1 % 8 != 0 || c0 + c1 > cin_pad)
+  // a 16-channel stage comes from one input: c0 and c1 are multiples of 16; TMA boxes start on
+  // 16-byte channel offsets and rows of whole 16-byte multiples
+  if (cout % 32 != 0 || cin_pad % 16 != 0 || c0 % 16 != 0 || c1 % 16 != 0 || c0 < 16 || c0 + c1 > cin_pad ||
+      (c1 && !in1))
     return cudaErrorInvalidValue;
+  if ((reinterpret_cast<uintptr_t>(in0) | reinterpret_cast<uintptr_t>(in1) | reinterpret_cast<uintptr_t>(w)) & 15)
+    return cudaErrorInvalidValue;
+  CUtensorMap tm0, tm1;
+  if (!activation_map(&tm0, in0, c0, up0 ? W / 2 : W, up0 ? H / 2 : H, N, up0 ? kHalfBox : kHX))
+    return cudaErrorInvalidValue;
+  if (c1) {
+    if (!activation_map(&tm1, in1, c1, W, H, N, kHX)) return cudaErrorInvalidValue;
+  } else {
+    tm1 = tm0;
+  }
   if ((fz.pool && (H % 2 || W % 2)) || (fz.head_w && conv_bn(cout) != cout)) return cudaErrorInvalidValue;
-  const dim3 grid((unsigned)(N * ((H + kTY - 1) / kTY) * ((W + kTX - 1) / kTX)), (unsigned)(cout / conv_bn(cout)));
-  // pipeline depth per column-block width (measured): 4 slots for 128 channels, 3 for 64, and
-  // for 32 channels 2 when the input has at most 32 channels (more blocks per SM), else 3
-  const int stages = (c0 + c1 + 15) / 16;
+  const int items = N * ((H + kTY - 1) / kTY) * ((W + kTX - 1) / kTX) * (cout / conv_bn(cout));
+  // pipeline depth per column-block width (measured on 256 crops of 256 x 256): 3 slots for 128
+  // channels (one block per SM), 2 for 64 and 32 (two and four blocks per SM)
   switch (conv_bn(cout)) {
-    case 128: launch_conv<128, 4>(grid, a, st); break;
-    case 64: launch_conv<64, 3>(grid, a, st); break;
-    default:
-      if (stages <= 2) launch_conv<32, 2>(grid, a, st);
-      else launch_conv<32, 3>(grid, a, st);
-      break;
+    case 128: launch_conv<128, 3>(items, tm0, tm1, a, u->n_sm, st); break;
+    case 64: launch_conv<64, 2>(items, tm0, tm1, a, u->n_sm, st); break;
+    default: launch_conv<32, 2>(items, tm0, tm1, a, u->n_sm, st); break;
   }
   return cudaGetLastError();
 }

@@ -85,6 +85,33 @@ def test_forward_and_gradients_match_float64_oracle(torch, H, W):
             assert rel < 0.03, (name, rel)
 
 
+def test_forward_at_crop_size_with_several_tiles_per_block(torch):
+    """Crops of 256 x 256 (the inference crop size), eight of them: the persistent convolution
+    blocks then each take several 16 x 16 tiles in turn (ring slots and both accumulator buffers
+    reused). Two of the crops are checked against the float64 oracle on the same bf16-rounded
+    weights and inputs; the inference widths (32, 64, 128, 128)."""
+    from paper_2309_16818_gb300 import mem as M
+    from paper_2309_16818_gb300.inpaint import init_params
+    widths = (32, 64, 128, 128)
+    rng = np.random.default_rng(4)
+    N, S = 8, 256
+    flat = init_params(2, 3, widths, out_scale=1.0)
+    x3 = rng.normal(size=(N, S, S, 3)).astype(np.float32)
+    fill = rng.normal(size=(N, S, S)).astype(np.float32)
+    net = M.UNet(3, widths)
+    net.set_params(torch.from_numpy(flat).cuda())
+    pred = net.forward(torch.from_numpy(x3).cuda(), torch.from_numpy(fill).cuda()).cpu().numpy()
+    net.check()
+    p = _unflatten(flat, 3, widths)
+    for k in p:
+        if k.endswith(".w") and k != "out.w":
+            p[k] = _bf16(p[k])
+    for i in (0, N - 1):
+        res, _ = U.forward(p, _bf16(x3[i:i + 1]), widths)
+        err = np.linalg.norm(pred[i] - (fill[i] + res[0])) / np.linalg.norm(res[0])
+        assert err < 2e-2, (i, err)
+
+
 def test_training_beats_diffusion_fill(torch, capsys):
     """Train on occlusion-hole crops for a few hundred Adam steps; on held-out crops the U-Net
     (diffusion fill + learned residual) must have a lower RMSE on the hidden cells than the
