@@ -127,7 +127,15 @@ __device__ __forceinline__ void mma_bf16_tc(u32 d_tmem, uint64_t ad, uint64_t bd
 __device__ __forceinline__ void mma_commit(u32 bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
-// 16 consecutive float32 columns of this thread's TMEM lane
+// 16 consecutive float32 columns of this thread's TMEM lane (complete after tmem_wait_ld)
+__device__ __forceinline__ void tmem_ld16_async(u32 taddr, u32 v[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tmem_ld16(u32 taddr, u32 v[16]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
@@ -201,7 +209,7 @@ template <int BN, int NST>
 struct ConvCfg {
   static constexpr int kWBytes = 9 * 2 * BN * 16;             // weights of one stage
   static constexpr int kSlot = 2 * kPlane + kWBytes + 2 * kStg;  // one pipeline slot
-  static constexpr int kSmem = NST * kSlot + 256 + 1024;      // + barriers, alignment slack
+  static constexpr int kSmem = NST * kSlot + 256 + 2048 + 1024;  // + barriers, bias and head, slack
   static constexpr int kCols = 4 * BN;                        // TMEM columns: 2 buffers x 2 halves
   static constexpr int kMaxBlocksPerSm = 512 / kCols;         // TMEM holds 512 columns
 };
@@ -221,6 +229,8 @@ __global__ void __launch_bounds__(256, ConvCfg<BN, NST>::kMaxBlocksPerSm)
   const u32 acce0 = accf0 + 16, done_bar = acce0 + 16;
   u32* tmem_slot = reinterpret_cast<u32*>(tail + 24 * NST + 40);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  float* sbias = reinterpret_cast<float*>(tail + 256);  // [256] bias of every output channel
+  float* shead = sbias + 256;                            // [256] 1x1 head weights
   const int tx = (a.W + kTX - 1) / kTX, ty = (a.H + kTY - 1) / kTY;
   const int NB = a.cout / BN;
   const int items = a.N * tx * ty * NB;
@@ -238,6 +248,10 @@ __global__ void __launch_bounds__(256, ConvCfg<BN, NST>::kMaxBlocksPerSm)
     mbar_init(done_bar, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  for (int i = tid; i < 256; i += 256) {  // output channels <= 256 wherever bias or head is given
+    sbias[i] = (a.bias && i < a.cout) ? a.bias[i] : 0.f;
+    shead[i] = (a.head_w && i < a.cout) ? a.head_w[i] : 0.f;
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
@@ -376,56 +390,60 @@ __global__ void __launch_bounds__(256, ConvCfg<BN, NST>::kMaxBlocksPerSm)
                           : nullptr;
         float hr = a.head_w ? a.head_b[0] : 0.f;
 #pragma unroll 1
-        for (int c0 = 0; c0 < BN; c0 += 16) {
-          u32 v[16];
-          tmem_ld16(tmem + ((u32)(q * 32) << 16) + (u32)(ab * 2 * BN + h * BN + c0), v);
-          u32 pk[8];
+        for (int c32 = 0; c32 < BN; c32 += 32) {
+          u32 v[2][16];
+          const u32 ta = tmem + ((u32)(q * 32) << 16) + (u32)(ab * 2 * BN + h * BN + c32);
+          tmem_ld16_async(ta, v[0]);
+          tmem_ld16_async(ta + 16, v[1]);
+          tmem_wait_ld();
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            float f0 = __uint_as_float(v[2 * j]), f1 = __uint_as_float(v[2 * j + 1]);
-            if (a.bias) {
-              f0 += a.bias[nb * BN + c0 + 2 * j];
-              f1 += a.bias[nb * BN + c0 + 2 * j + 1];
-            }
-            if (a.relu) {
-              f0 = fmaxf(f0, 0.f);
-              f1 = fmaxf(f1, 0.f);
-            }
-            __nv_bfloat162 p2 = __floats2bfloat162_rn(f0, f1);
-            pk[j] = *reinterpret_cast<u32*>(&p2);
-          }
-          if (inside && a.store) {
-            uint4* dst = reinterpret_cast<uint4*>(o + c0);
-            dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-            dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
-          }
-          if (po) {
-            u32 mx[8];
+          for (int k = 0; k < 2; ++k) {
+            const int c0 = c32 + 16 * k;
+            const float* bz = sbias + nb * BN + c0;
+            u32 pk[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-              const u32 o1 = __shfl_xor_sync(0xffffffffu, pk[j], 1);
-              const u32 o8 = __shfl_xor_sync(0xffffffffu, pk[j], 8);
-              const u32 o9 = __shfl_xor_sync(0xffffffffu, pk[j], 9);
-              const float2 a0 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&pk[j]));
-              const float2 a1 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&o1));
-              const float2 a8 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&o8));
-              const float2 a9 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&o9));
-              __nv_bfloat162 r2 = __floats2bfloat162_rn(fmaxf(fmaxf(a0.x, a1.x), fmaxf(a8.x, a9.x)),
-                                                        fmaxf(fmaxf(a0.y, a1.y), fmaxf(a8.y, a9.y)));
-              mx[j] = *reinterpret_cast<u32*>(&r2);
+              float f0 = __uint_as_float(v[k][2 * j]) + bz[2 * j], f1 = __uint_as_float(v[k][2 * j + 1]) + bz[2 * j + 1];
+              if (a.relu) {
+                f0 = fmaxf(f0, 0.f);
+                f1 = fmaxf(f1, 0.f);
+              }
+              __nv_bfloat162 p2 = __floats2bfloat162_rn(f0, f1);
+              pk[j] = *reinterpret_cast<u32*>(&p2);
             }
-            if (pool_writer) {
-              uint4* dst = reinterpret_cast<uint4*>(po + c0);
-              dst[0] = make_uint4(mx[0], mx[1], mx[2], mx[3]);
-              dst[1] = make_uint4(mx[4], mx[5], mx[6], mx[7]);
+            if (inside && a.store) {
+              uint4* dst = reinterpret_cast<uint4*>(o + c0);
+              dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+              dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
             }
-          }
-          if (a.head_w) {
+            if (po) {
+              u32 mx[8];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&pk[j]));
-              hr = fmaf(f.x, a.head_w[c0 + 2 * j], hr);
-              hr = fmaf(f.y, a.head_w[c0 + 2 * j + 1], hr);
+              for (int j = 0; j < 8; ++j) {
+                const u32 o1 = __shfl_xor_sync(0xffffffffu, pk[j], 1);
+                const u32 o8 = __shfl_xor_sync(0xffffffffu, pk[j], 8);
+                const u32 o9 = __shfl_xor_sync(0xffffffffu, pk[j], 9);
+                const float2 a0 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&pk[j]));
+                const float2 a1 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&o1));
+                const float2 a8 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&o8));
+                const float2 a9 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&o9));
+                __nv_bfloat162 r2 = __floats2bfloat162_rn(fmaxf(fmaxf(a0.x, a1.x), fmaxf(a8.x, a9.x)),
+                                                          fmaxf(fmaxf(a0.y, a1.y), fmaxf(a8.y, a9.y)));
+                mx[j] = *reinterpret_cast<u32*>(&r2);
+              }
+              if (pool_writer) {
+                uint4* dst = reinterpret_cast<uint4*>(po + c0);
+                dst[0] = make_uint4(mx[0], mx[1], mx[2], mx[3]);
+                dst[1] = make_uint4(mx[4], mx[5], mx[6], mx[7]);
+              }
+            }
+            if (a.head_w) {
+#pragma unroll
+              for (int j = 0; j < 8; ++j) {
+                const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&pk[j]));
+                hr = fmaf(f.x, shead[c0 + 2 * j], hr);
+                hr = fmaf(f.y, shead[c0 + 2 * j + 1], hr);
+              }
             }
           }
         }
@@ -930,6 +948,7 @@ cudaError_t conv(mem_unet* u, const ConvLayer& c, const bf16* in0, const bf16* i
     tm1 = tm0;
   }
   if ((fz.pool && (H % 2 || W % 2)) || (fz.head_w && conv_bn(cout) != cout)) return cudaErrorInvalidValue;
+  if ((bias || fz.head_w) && cout > 256) return cudaErrorInvalidValue;  // staged in 256-entry tables
   const int items = N * ((H + kTY - 1) / kTY) * ((W + kTX - 1) / kTX) * (cout / conv_bn(cout));
   // pipeline depth per column-block width (measured on 256 crops of 256 x 256): 3 slots for 128
   // channels (one block per SM), 2 for 64 and 32 (two and four blocks per SM)
