@@ -14,6 +14,11 @@ Parity status of each function (what pins it in ``tests/test_oracle_*.py``):
   Bresenham path properties in all 8 octants, dense float64 ray march on small maps
 * ``move``         shift + inverse shift, fuse-then-move == move-then-fuse
 * ``harmonic_fill`` linear fields and constants reproduced, maximum principle
+
+``tests/test_oracle_mutants.py`` builds copies of this oracle (and of ``unet.py``) with one
+planted mistake each -- a dropped term, a wrong sign, a transposed index, swapped weights -- and
+requires the pins above to fail on every one. ``tests/golden/make_golden.py`` writes the stored
+expected values of ``tests/golden/fusion_w12.json`` from this oracle alone.
 """
 from __future__ import annotations
 
@@ -35,7 +40,10 @@ MAX_SRC_LAYERS = 8
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (no contraction of a*b+c, no fast-math)."""
+    """Compile the oracle with gcc (no contraction of a*b+c, no fast-math). MEM_ORACLE_LIB names
+    an already built copy to load instead (the planted-mistake tests build altered copies)."""
+    if os.environ.get("MEM_ORACLE_LIB"):
+        return os.environ["MEM_ORACLE_LIB"]
     newest = max(os.path.getmtime(p) for p in SRC + [os.path.join(HERE, "mem_oracle.h")])
     if force or not os.path.exists(LIB_PATH) or os.path.getmtime(LIB_PATH) < newest:
         tmp = LIB_PATH + f".tmp{os.getpid()}"

@@ -1,0 +1,132 @@
+"""Planted mistakes: copies of the C oracle, each with one plausible error (a dropped term, a
+wrong sign, a transposed index, swapped weights, an argmin for an argmax), must each fail the
+oracle's pins in test_oracle_points.py and test_oracle_image_move.py -- so the pins would catch
+that class of mistake in the oracle itself. The unaltered copy, built the same way, must pass.
+CPU only; the altered copies live in a temporary folder."""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+ORACLE = os.path.join(ROOT, "oracle")
+PINS = [os.path.join(ROOT, "tests", "test_oracle_points.py"),
+        os.path.join(ROOT, "tests", "test_oracle_image_move.py")]
+
+# name -> [(exact source text, replacement)], each text occurring once in mem_oracle.c
+MUTANTS = {
+    "cell index transposed": [("*cell = iy * c->W + ix;", "*cell = ix * c->W + iy;")],
+    "range term of the measurement noise dropped (Sec. III-B)":
+        [("float sm = fmaf(c->sigma1, rs, c->sigma0);", "float sm = c->sigma0;")],
+    "gate without the cell variance": [("float rhs = lam2 * (vj + vm);", "float rhs = lam2 * vm;")],
+    "gate with lambda instead of lambda^2":
+        [("float lam2 = c->gate_lambda * c->gate_lambda;", "float lam2 = c->gate_lambda;")],
+    "Kalman mean: prior not weighted by its information":
+        [("(s->h[j] / s->var[j] + Swz[j]) / P", "(s->h[j] + Swz[j]) / P")],
+    "Kalman variance: prior information dropped":
+        [("s->var[j] = store_round(c, ORC_F32, 1.0 / P);", "s->var[j] = store_round(c, ORC_F32, 1.0 / Sw[j]);")],
+    "average rule returns the sum (Eq. 1)":
+        [("th[j * C + k] = store_round(c, fmt, S[k] / N);", "th[j * C + k] = store_round(c, fmt, S[k]);")],
+    "exponential averaging weights swapped (Eq. 2)":
+        [("c->w[l] * a + (1.0 - c->w[l]) * th[j * C + k]", "(1.0 - c->w[l]) * a + c->w[l] * th[j * C + k]")],
+    "Gaussian mean weights swapped (Eq. 6)":
+        [("mu = sf2 / den * mu0 + N * s02 / den * mu_ml;", "mu = N * s02 / den * mu0 + sf2 / den * mu_ml;")],
+    "Gaussian variance without the prior (Eq. 7)": [("s2 = sf2 * s02 / den;", "s2 = sf2 / den;")],
+    "Dirichlet adds the mean instead of the sum (Eq. 12)":
+        [("store_round(c, fmt, th[j * C + k] + S[k])", "store_round(c, fmt, th[j * C + k] + S[k] / N)")],
+    "class max takes the minimum": [("double best = -INFINITY;", "double best = INFINITY;"),
+                                    ("if (M[k] > best) {", "if (M[k] < best) {")],
+    "pixel truncated instead of rounded": [("float fu = floorf(u + 0.5f), fv = floorf(v + 0.5f);",
+                                            "float fu = floorf(u), fv = floorf(v);")],
+    "ray height slope with the wrong sign": [("float ray = fmaf(tq, hz - hc, hc);", "float ray = fmaf(tq, hc - hz, hc);")],
+    "pixel index transposed": [("int64_t p = (int64_t)py * Wi + px;", "int64_t p = (int64_t)px * H + py;")],
+    "visibility test not strict": [("if ((float)h0[q] >= ray) {", "if ((float)h0[q] > ray + 1.0f) {")],
+    "map move shifts the wrong way": [("long oy = iy + sy;", "long oy = iy - sy;")],
+}
+
+
+def _build(tmp, name, subs):
+    d = os.path.join(tmp, name.replace(" ", "_").replace("/", "_")[:40])
+    os.makedirs(d, exist_ok=True)
+    shutil.copy(os.path.join(ORACLE, "mem_oracle.h"), d)
+    src = open(os.path.join(ORACLE, "mem_oracle.c")).read()
+    for old, new in subs:
+        assert src.count(old) == 1, (name, old)
+        src = src.replace(old, new)
+    with open(os.path.join(d, "mem_oracle.c"), "w") as f:
+        f.write(src)
+    lib = os.path.join(d, "liboracle.so")
+    subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-o", lib,
+                           os.path.join(d, "mem_oracle.c"), "-lm"])
+    return lib
+
+
+def _pins(lib):
+    env = dict(os.environ, MEM_ORACLE_LIB=lib)
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider"] + PINS,
+                       cwd=ROOT, env=env, capture_output=True, text=True)
+    return r.returncode, r.stdout[-2000:]
+
+
+def test_unaltered_copy_passes_the_pins(tmp_path):
+    rc, out = _pins(_build(str(tmp_path), "unaltered", []))
+    assert rc == 0, out
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_planted_mistake_fails_a_pin(tmp_path, name):
+    rc, out = _pins(_build(str(tmp_path), name, MUTANTS[name]))
+    assert rc == 1, f"{name}: the pins did not fail (exit {rc})\n{out}"
+
+
+# the float64 U-Net oracle (oracle/unet.py): name -> (exact source text, replacement)
+UNET_MUTANTS = {
+    "im2col tap order transposed": ("for ky in range(3) for kx in range(3)]", "for kx in range(3) for ky in range(3)]"),
+    "col2im overwrites overlapping taps": ("xp[:, ky:ky + H, kx:kx + W, :] += cols[:, :, :, t, :]",
+                                          "xp[:, ky:ky + H, kx:kx + W, :] = cols[:, :, :, t, :]"),
+    "convolution bias dropped": ("y = im2col(x) @ w.reshape(-1, w.shape[3]) + b", "y = im2col(x) @ w.reshape(-1, w.shape[3])"),
+    "upsample gradient averaged": ("return dy.reshape(N, H // 2, 2, W // 2, 2, C).sum(axis=(2, 4))",
+                                   "return dy.reshape(N, H // 2, 2, W // 2, 2, C).mean(axis=(2, 4))"),
+    "max-pool gradient to the minimum": ("am = v.argmax(axis=4)", "am = v.argmin(axis=4)"),
+    "loss gradient without the factor 2": ("2.0 * diff / cnt", "diff / cnt"),
+    "ReLU gradient mask dropped": ('dt = dt * (a[name + ".out"] > 0)', "dt = dt"),
+    "skip concatenation order swapped in the forward pass": ("np.concatenate([upsample(e4), e3], axis=3)",
+                                                             "np.concatenate([e3, upsample(e4)], axis=3)"),
+    "head bias dropped": ('out = d1 @ p["out.w"] + p["out.b"]', 'out = d1 @ p["out.w"]'),
+}
+
+_RUN_UNET = r'''
+import sys, types
+sys.path.insert(0, ROOT)
+import oracle
+src = open(ROOT + "/oracle/unet.py").read()
+if OLD:
+    assert src.count(OLD) == 1, OLD
+    src = src.replace(OLD, NEW)
+m = types.ModuleType("oracle.unet")
+m.__file__ = ROOT + "/oracle/unet.py"
+exec(compile(src, m.__file__, "exec"), m.__dict__)
+sys.modules["oracle.unet"] = m
+oracle.unet = m
+import pytest
+sys.exit(pytest.main(["-x", "-q", "-p", "no:cacheprovider", ROOT + "/tests/test_oracle_unet.py"]))
+'''
+
+
+def _unet_pins(old, new):
+    code = f"ROOT = {ROOT!r}\nOLD = {old!r}\nNEW = {new!r}\n" + _RUN_UNET
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True)
+    return r.returncode, r.stdout[-2000:] + r.stderr[-2000:]
+
+
+def test_unaltered_unet_oracle_passes_the_pins():
+    rc, out = _unet_pins("", "")
+    assert rc == 0, out
+
+
+@pytest.mark.parametrize("name", sorted(UNET_MUTANTS))
+def test_planted_unet_mistake_fails_a_pin(name):
+    rc, out = _unet_pins(*UNET_MUTANTS[name])
+    assert rc == 1, f"{name}: the pins did not fail (exit {rc})\n{out}"
