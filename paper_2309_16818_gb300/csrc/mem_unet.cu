@@ -3,16 +3,16 @@
 //
 // Layout: activations NHWC bf16. A 3x3 convolution is an implicit GEMM
 // C[pixels, cout] = A[pixels, 9*cin] B[9*cin, cout] on the tcgen05 tensor
-// cores: a block gathers the input halo of a 16 x 16 output tile (16
-// channels per pipeline stage, cp.async, zero fill at the border) and the
-// stage's packed weights (one bulk copy) into shared memory, one thread issues
-// the MMAs of all nine taps from that one halo (descriptors offset per tap),
-// and the float32 accumulator lives in tensor memory until the epilogue. The
-// decoder's nearest-neighbour upsampling and channel concatenation are folded
-// into the gather (two input tensors, the first at half resolution). The data
-// gradient is the same kernel with flipped, transposed weights; the weight
-// gradient is a GEMM over pixels split across blocks with float32 atomics
-// (warp-level mma.sync).
+// cores: TMA box loads bring the input halo of a 16 x 16 output tile (16
+// channels per pipeline stage, zero outside the image) and one bulk copy the
+// stage's packed weights into shared memory; one thread issues the MMAs of all
+// nine taps from that one halo (descriptors offset per tap), and the float32
+// accumulator lives in tensor memory until the epilogue. The decoder's
+// concatenation is a choice of tensor map and its nearest upsampling a
+// half-resolution box replicated in shared memory. The data gradient is the
+// same kernel with flipped, transposed weights; the weight gradient is a
+// tcgen05 GEMM over pixels (both operands MN-major from TMA-loaded planes, one
+// TMEM accumulator per tap) split across blocks with float32 atomics.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <math.h>
@@ -27,30 +27,10 @@ typedef __nv_bfloat16 bf16;
 namespace memk {
 
 // ---------------------------------------------------------------------------
-// tensor-core helpers (PTX)
+// PTX helpers
 
 __device__ __forceinline__ u32 smem_u32(const void* p) {
   return (u32)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid) {
-  const int n = valid ? 16 : 0;  // zero fill when not valid
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(dst)), "l"(src), "r"(n));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
-
-__device__ __forceinline__ void ldsm_x4_t(u32 r[4], const void* p) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(smem_u32(p)));
-}
-__device__ __forceinline__ void mma_bf16(float d[4], const u32 a[4], u32 b0, u32 b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
 // ---------------------------------------------------------------------------
@@ -97,14 +77,6 @@ __device__ __forceinline__ void tma_load_4d(u32 dst, const CUtensorMap* map, int
       "[%6];" ::"r"(dst),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(c), "r"(x), "r"(y), "r"(n), "r"(bar)
       : "memory");
-}
-__device__ __forceinline__ void cp_async16s(u32 dst, const void* src, bool valid) {
-  const int n = valid ? 16 : 0;
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(n) : "memory");
-}
-template <int N>
-__device__ __forceinline__ void cp_async_wait_n() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -464,114 +436,158 @@ __global__ void __launch_bounds__(256, ConvCfg<BN, NST>::kMaxBlocksPerSm)
 }
 
 // ---------------------------------------------------------------------------
-// weight gradient: dW[t][ci][co] += sum_p A[p, (t, ci)] dY[p, co]
+// weight gradient: dW[t][ci][co] = sum_p X[p + off(t)][ci] dY[p][co]
+//
+// On the tensor cores with both operands read MN-major straight from TMA-loaded
+// planes: per 16 x 8 tile of output pixels, the 18 x 10 input halo arrives as
+// up to 16 planes of 8 channels (the block's 128 input channels = M) and dY as
+// NB/8 planes of 8 output channels (N); a K = 16 step is one 16-pixel row, so
+// tap (dy, dx) and row py read the halo through a descriptor offset by
+// ((py + dy) * 18 + dx) pixels, 128 bytes between the two 8-pixel halves of K
+// and one plane between 8-channel groups of M (and N). Each tap of the block's
+// tap group accumulates in its own TMEM columns over all tiles of the block's
+// pixel range; the epilogue adds the float32 sums to dW with atomics (blocks
+// split the pixels). Warp 0: TMEM and the MMA thread; warp 1: one thread
+// issues the copies; all four warps drain TMEM at the end. Waits are bounded.
 
 struct WgradArgs {
-  const bf16* in0;
-  const bf16* in1;
-  int c0, c1, up0, cin_pad;
-  const bf16* dy;  // [P, cout]
-  float* dw;       // [9][cin_pad][cout] float32
-  int cout, N, H, W;
-  int64_t pix_per_split;
+  int Cx, cin_pad, cout;  // input channels in the tensor (real), rows of dW per tap, dY channels
+  float* dw;              // [9][cin_pad][cout] float32, accumulated into
+  int N, H, W;
+  int tiles;              // 16 x 8 pixel tiles over the batch
+  int* err;
 };
 
-template <int BN>
-__global__ void __launch_bounds__(128) k_wgrad3x3(WgradArgs a) {
-  constexpr int kBpad = BN + 8;
-  __shared__ __align__(16) bf16 Xs[2][32][40];      // [pixel][ci]
-  __shared__ __align__(16) bf16 Ds[2][32][kBpad];   // [pixel][co]
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int wm = warp >> 1, wn = warp & 1;  // warp tile: 16 ci x BN/2 co
-  const int kchunks = a.cin_pad / 32;
-  const int t = blockIdx.y / kchunks, cb = (blockIdx.y - t * kchunks) * 32;
-  const int n0 = blockIdx.z * BN;
-  const int dy = t / 3 - 1, dx = t % 3 - 1;
-  const int64_t P = (int64_t)a.N * a.H * a.W;
-  const int64_t p_begin = (int64_t)blockIdx.x * a.pix_per_split;
-  const int64_t p_end = min(P, p_begin + a.pix_per_split);
-  const int HW = a.H * a.W;
-  constexpr int NT = BN / 16;
-  float acc[NT][4];
+constexpr int kWgPlane = 2944;          // one 18 x 10 x 8-channel halo plane (2880 bytes), 128-byte stride
+constexpr int kWgPlaneBytes = 18 * 10 * 16;
+constexpr int kWgDyPlane = 16 * 8 * 16;  // one 16 x 8 x 8-channel dY plane (2048 bytes)
+
+template <int NB, int TAPG, int NST>
+struct WgCfg {
+  static constexpr int kSlot = 16 * kWgPlane + (NB / 8) * kWgDyPlane;
+  static constexpr int kSmem = NST * kSlot + 128 + 1024;  // + barriers, alignment slack
+};
+
+template <int NB, int TAPG, int NST>
+__global__ void __launch_bounds__(128, 1)
+    k_wgrad3x3t(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmy, WgradArgs a) {
+  using C = WgCfg<NB, TAPG, NST>;
+  extern __shared__ __align__(1024) unsigned char sm_raw[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const u32 sbase = (smem_u32(sm_raw) + 1023u) & ~1023u;
+  unsigned char* tail = sm_raw + (sbase - smem_u32(sm_raw)) + NST * C::kSlot;
+  const u32 bar0 = sbase + NST * C::kSlot;
+  const u32 full0 = bar0, empty0 = bar0 + 8 * NST, done_bar = bar0 + 16 * NST;
+  u32* tmem_slot = reinterpret_cast<u32*>(tail + 16 * NST + 8);
+  const int mb = blockIdx.y;                                  // input channels mb*128 ..
+  const int nb = blockIdx.z % (a.cout / NB), tg = blockIdx.z / (a.cout / NB);  // output block, tap group
+  const int t_first = tg * TAPG, n_taps = min(TAPG, 9 - t_first);
+  const int t_begin = (int)((int64_t)blockIdx.x * a.tiles / gridDim.x);
+  const int t_end = (int)((int64_t)(blockIdx.x + 1) * a.tiles / gridDim.x);
+  const int nt = t_end - t_begin;
+  const int planes = min(16, (a.Cx - mb * 128 + 7) / 8);  // halo planes holding real channels (> 0)
+  const int tx = (a.W + 15) / 16, ty = (a.H + 7) / 8;
+  if (tid == 0) {
+    for (int s = 0; s < NST; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    mbar_init(done_bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const u32 tmem = *tmem_slot;
+  bool ok = true;
+  if (warp == 0 && lane == 0) {
+    // f32 accumulator, bf16 A and B, both MN-major, N = NB, M = 128
+    const u32 idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) | ((u32)(NB >> 3) << 17) |
+                      ((u32)(128 >> 4) << 24);
+    for (int it = 0; it < nt; ++it) {
+      const int slot = it % NST;
+      if (!mbar_wait(full0 + 8 * slot, (it / NST) & 1, a.err)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const u32 hb = sbase + slot * C::kSlot, yb = hb + 16 * kWgPlane;
+      for (int tl = 0; tl < n_taps; ++tl) {
+        const int t = t_first + tl, dy = t / 3, dx = t % 3;
 #pragma unroll
-  for (int j = 0; j < NT; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-  auto stage = [&](int64_t pb, int buf) {
-    // X: 32 pixels x 32 channels = 128 chunks, one per thread
-    {
-      const int r = tid >> 2, ck = tid & 3;
-      const int64_t p = pb + r;
-      bool ok = p < p_end;
-      const int64_t pp = ok ? p : 0;
-      const int n = (int)(pp / HW);
-      const int rem = (int)(pp - (int64_t)n * HW);
-      const int yy = rem / a.W + dy, xx = rem % a.W + dx;
-      const int ci = cb + 8 * ck;
-      ok = ok && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W && ci < a.c0 + a.c1;
-      const bf16* src = a.in0;
-      if (ok) {
-        if (ci < a.c0) {
-          if (a.up0) {
-            const int Hh = a.H >> 1, Wh = a.W >> 1;
-            src = a.in0 + (((int64_t)n * Hh + (yy >> 1)) * Wh + (xx >> 1)) * a.c0 + ci;
-          } else {
-            src = a.in0 + (((int64_t)n * a.H + yy) * a.W + xx) * a.c0 + ci;
-          }
-        } else {
-          src = a.in1 + (((int64_t)n * a.H + yy) * a.W + xx) * a.c1 + (ci - a.c0);
+        for (int py = 0; py < 8; ++py) {
+          const uint64_t ad = sdesc(hb + ((py + dy) * 18 + dx) * 16, 128, kWgPlane);
+          const uint64_t bd = sdesc(yb + py * 16 * 16, 128, kWgDyPlane);
+          mma_bf16_tc(tmem + (u32)(tl * NB), ad, bd, idesc, (it | py) != 0);
         }
       }
-      cp_async16(&Xs[buf][r][8 * ck], src, ok);
+      mma_commit(empty0 + 8 * slot);
     }
-    // dY: 32 pixels x BN channels
-    constexpr int CPR = BN / 8;
-#pragma unroll
-    for (int i = 0; i < (32 * CPR) / 128; ++i) {
-      const int c = tid + 128 * i;
-      const int r = c / CPR, cc = c - r * CPR;
-      const int64_t p = pb + r;
-      const bool ok = p < p_end;
-      cp_async16(&Ds[buf][r][8 * cc], a.dy + (ok ? p : 0) * a.cout + n0 + 8 * cc, ok);
-    }
-    cp_async_commit();
-  };
-  if (p_begin < p_end) {
-    stage(p_begin, 0);
-    int buf = 0;
-    for (int64_t pb = p_begin; pb < p_end; pb += 32) {
-      if (pb + 32 < p_end) {
-        stage(pb + 32, buf ^ 1);
-        cp_async_wait1();
-      } else {
-        cp_async_wait0();
-      }
-      __syncthreads();
-#pragma unroll
-      for (int kk = 0; kk < 32; kk += 16) {
-        // A = X^T: rows ci, columns pixels -> transposed load of the [pixel][ci] tile
-        u32 af[4];
-        ldsm_x4_t(af, &Xs[buf][kk + (lane & 7) + (lane >> 4) * 8][wm * 16 + ((lane >> 3) & 1) * 8]);
-#pragma unroll
-        for (int np = 0; np < NT / 2; ++np) {
-          u32 bfr[4];
-          ldsm_x4_t(bfr, &Ds[buf][kk + (lane & 7) + ((lane >> 3) & 1) * 8][wn * (BN / 2) + np * 16 + (lane >> 4) * 8]);
-          mma_bf16(acc[2 * np], af, bfr[0], bfr[1]);
-          mma_bf16(acc[2 * np + 1], af, bfr[2], bfr[3]);
-        }
-      }
-      __syncthreads();
-      buf ^= 1;
+    mma_commit(done_bar);
+  } else if (warp == 1 && lane == 0) {
+    for (int it = 0; it < nt; ++it) {
+      const int slot = it % NST;
+      if (it >= NST && !mbar_wait(empty0 + 8 * slot, ((it / NST) - 1) & 1, a.err)) break;
+      int b = t_begin + it;
+      const int n = b / (tx * ty);
+      b -= n * tx * ty;
+      const int y0 = (b / tx) * 8, x0 = (b % tx) * 16;
+      const u32 hb = sbase + slot * C::kSlot, yb = hb + 16 * kWgPlane;
+      mbar_arrive_tx(full0 + 8 * slot, (u32)(planes * kWgPlaneBytes + (NB / 8) * kWgDyPlane));
+      for (int pl = 0; pl < planes; ++pl)
+        tma_load_4d(hb + pl * kWgPlane, &tmx, mb * 128 + pl * 8, x0 - 1, y0 - 1, n, full0 + 8 * slot);
+      for (int j = 0; j < NB / 8; ++j)
+        tma_load_4d(yb + j * kWgDyPlane, &tmy, nb * NB + j * 8, x0, y0, n, full0 + 8 * slot);
     }
   }
+  // all MMAs of this block done (bounded); then every thread owns TMEM lane tid = input channel
+  ok = mbar_wait(done_bar, 0, a.err) && ok;
+  tc_fence_after();
+  ok = __all_sync(0xffffffffu, ok) && nt > 0;
+  const int ci = mb * 128 + tid;
+  if (ok) {
+    for (int tl = 0; tl < n_taps; ++tl) {
+      const int t = t_first + tl;
+#pragma unroll 1
+      for (int c0 = 0; c0 < NB; c0 += 16) {
+        u32 v[16];
+        tmem_ld16(tmem + ((u32)(warp * 32) << 16) + (u32)(tl * NB + c0), v);
+        if (ci < a.Cx && ci < a.cin_pad) {
+          float* d = a.dw + ((int64_t)t * a.cin_pad + ci) * a.cout + nb * NB + c0;
 #pragma unroll
-  for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int ci = cb + wm * 16 + (lane >> 2) + 8 * h;
-      const int co = n0 + wn * (BN / 2) + nt * 8 + (lane & 3) * 2;
-      float* d = a.dw + ((int64_t)(t * a.cin_pad + ci) * a.cout + co);
-      atomicAdd(d, acc[nt][2 * h]);
-      atomicAdd(d + 1, acc[nt][2 * h + 1]);
+          for (int j = 0; j < 16; ++j) atomicAdd(d + j, __uint_as_float(v[j]));
+        }
+      }
     }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+  }
+}
+
+// decoder input for the weight gradient: [upsampled in0 (c0), in1 (c1)] at full resolution
+__global__ void k_cat_up(const bf16* __restrict__ in0, const bf16* __restrict__ in1, bf16* __restrict__ out, int N,
+                         int H, int W, int c0, int c1) {
+  const int cin = c0 + c1, chunks = cin / 8;
+  const int64_t total = (int64_t)N * H * W * chunks;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int ch = (int)(i % chunks) * 8;
+    const int64_t p = i / chunks;
+    const int x = (int)(p % W), y = (int)((p / W) % H), n = (int)(p / ((int64_t)W * H));
+    const uint4* src = ch < c0 ? reinterpret_cast<const uint4*>(
+                                     in0 + (((int64_t)n * (H / 2) + y / 2) * (W / 2) + x / 2) * c0 + ch)
+                               : reinterpret_cast<const uint4*>(in1 + p * c1 + (ch - c0));
+    *reinterpret_cast<uint4*>(out + p * cin + ch) = *src;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -643,18 +659,45 @@ __global__ void k_split_cat_bwd(const bf16* __restrict__ dcat, bf16* __restrict_
 }
 
 // bias gradient: db[c] += sum over pixels of dy[p][c]
+// bias gradient db[c] += sum_p dy[p][c]: a thread owns one 8-channel chunk (16-byte loads) over
+// a stride of pixels; partial sums meet in shared memory, one atomic per channel per block
 __global__ void k_bias_grad(const bf16* __restrict__ dy, float* __restrict__ db, int64_t P, int C) {
-  const int c = threadIdx.x % C, lanes = blockDim.x / C;
-  const int sub = threadIdx.x / C;
-  if (sub >= lanes) return;
-  float s = 0.f;
-  for (int64_t p = (int64_t)blockIdx.x * lanes + sub; p < P; p += (int64_t)gridDim.x * lanes)
-    s += __bfloat162float(dy[p * C + c]);
-  atomicAdd(&db[c], s);
+  __shared__ float s_db[256];
+  for (int c = threadIdx.x; c < C; c += blockDim.x) s_db[c] = 0.f;
+  __syncthreads();
+  const int chunks = C / 8;  // divides the grid's thread count, so a thread keeps its chunk
+  const int64_t items = P * chunks, stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  for (int64_t i = i0; i < items; i += stride) {
+    const uint4 v = *reinterpret_cast<const uint4*>(dy + i * 8);
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float2 f = __bfloat1622float2(h[j]);
+      acc[2 * j] += f.x;
+      acc[2 * j + 1] += f.y;
+    }
+  }
+  if (i0 < items) {
+    const int k = (int)(i0 % chunks) * 8;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) atomicAdd(&s_db[k + j], acc[j]);
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < C; c += blockDim.x) atomicAdd(&db[c], s_db[c]);
+}
+
+__device__ __forceinline__ float warp_sum(float x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
 }
 
 // final 1x1 convolution (residual over the diffusion fill), masked-MSE loss and
-// its gradients: res = b + d1 . w ; pred = fill + res
+// its gradients: res = b + d1 . w ; pred = fill + res. A thread owns a pixel and reads
+// its channels 8 at a time; the weight gradient is summed across the warp by shuffles
+// (one shared-memory add per warp and channel), skipped where no lane has a hidden cell.
 __global__ void k_head(const bf16* __restrict__ d1, int C, const float* __restrict__ w, const float* __restrict__ b,
                        const float* __restrict__ fill, float* __restrict__ pred, const float* __restrict__ target,
                        const uint8_t* __restrict__ hidden, float inv_cnt, int64_t P, float* __restrict__ loss,
@@ -667,20 +710,58 @@ __global__ void k_head(const bf16* __restrict__ d1, int C, const float* __restri
   }
   if (threadIdx.x == 0) s_loss = s_db = 0.f;
   __syncthreads();
+  const int lane = threadIdx.x & 31;
   float l = 0.f, gb = 0.f;
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
-    float r = b[0];
-    for (int c = 0; c < C; ++c) r = fmaf(__bfloat162float(d1[p * C + c]), s_w[c], r);
-    const float pr = fill[p] + r;
-    if (pred) pred[p] = pr;
-    if (target) {
-      const float diff = hidden[p] ? pr - target[p] : 0.f;
-      l += diff * diff;
-      const float g = 2.f * diff * inv_cnt;
-      gb += g;
-      for (int c = 0; c < C; ++c) {
-        dd1[p * C + c] = __float2bfloat16_rn(g * s_w[c]);
-        atomicAdd(&s_dw[c], g * __bfloat162float(d1[p * C + c]));
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  // every lane of a warp runs the same number of iterations (the shuffles need all 32)
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < P; base += stride) {
+    const int64_t p = base + threadIdx.x;
+    const bool in = p < P;
+    float g = 0.f;
+    if (in) {
+      float r = b[0];
+      for (int c = 0; c < C; c += 8) {
+        const uint4 v = *reinterpret_cast<const uint4*>(d1 + p * C + c);
+        const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float2 f = __bfloat1622float2(h[j]);
+          r = fmaf(f.x, s_w[c + 2 * j], r);
+          r = fmaf(f.y, s_w[c + 2 * j + 1], r);
+        }
+      }
+      const float pr = fill[p] + r;
+      if (pred) pred[p] = pr;
+      if (target) {
+        const float diff = hidden[p] ? pr - target[p] : 0.f;
+        l += diff * diff;
+        g = 2.f * diff * inv_cnt;
+        gb += g;
+        for (int c = 0; c < C; c += 8) {
+          u32 o[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            __nv_bfloat162 q = __floats2bfloat162_rn(g * s_w[c + 2 * j], g * s_w[c + 2 * j + 1]);
+            o[j] = *reinterpret_cast<u32*>(&q);
+          }
+          *reinterpret_cast<uint4*>(dd1 + p * C + c) = make_uint4(o[0], o[1], o[2], o[3]);
+        }
+      }
+    }
+    if (target && __any_sync(0xffffffffu, g != 0.f)) {
+      for (int c = 0; c < C; c += 8) {
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (in) v = *reinterpret_cast<const uint4*>(d1 + p * C + c);
+        const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float2 f = __bfloat1622float2(h[j]);
+          const float s0 = warp_sum(g * f.x), s1 = warp_sum(g * f.y);
+          if (lane == 0) {
+            atomicAdd(&s_dw[c + 2 * j], s0);
+            atomicAdd(&s_dw[c + 2 * j + 1], s1);
+          }
+        }
       }
     }
   }
@@ -960,35 +1041,69 @@ cudaError_t conv(mem_unet* u, const ConvLayer& c, const bf16* in0, const bf16* i
   return cudaGetLastError();
 }
 
+template <int NB, int TAPG, int NST>
+void launch_wgrad(dim3 grid, const CUtensorMap& tmx, const CUtensorMap& tmy, const WgradArgs& a, cudaStream_t st) {
+  using C = WgCfg<NB, TAPG, NST>;
+  static bool attr = false;  // dynamic shared memory above 48 KB is opted into once
+  if (!attr) {
+    cudaFuncSetAttribute(k_wgrad3x3t<NB, TAPG, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
+    attr = true;
+  }
+  k_wgrad3x3t<NB, TAPG, NST><<<grid, 128, C::kSmem, st>>>(tmx, tmy, a);
+}
+
+// NHWC bf16 tensor [n][h][w][c] as a 4-D tensor map with boxes of 8 channels x bw x bh pixels
+bool nhwc_map(CUtensorMap* m, const bf16* base, int c, int w, int h, int n, int bw, int bh) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[4] = {(cuuint64_t)c, (cuuint64_t)w, (cuuint64_t)h, (cuuint64_t)n};
+  const cuuint64_t strides[3] = {(cuuint64_t)c * 2, (cuuint64_t)c * 2 * w, (cuuint64_t)c * 2 * w * h};
+  const cuuint32_t boxd[4] = {8, (cuuint32_t)bw, (cuuint32_t)bh, 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(base), dims, strides, boxd, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// dW (float32, [9][cin_pad][cout], accumulated into) of one 3x3 convolution whose input is
+// in0 (c0 channels; at half resolution when up0) concatenated with in1 (c1 channels)
 cudaError_t wgrad(mem_unet* u, const ConvLayer& c, const bf16* in0, const bf16* in1, const bf16* dy,
                   float* dw_pad, int N, int H, int W, cudaStream_t st) {
+  const bf16* X = in0;
+  int Cx = c.c0;
+  if (c.c1 || c.up0) {  // decoder input: materialise [upsampled, skip] in the concat scratch
+    Cx = c.c0 + c.c1;
+    k_cat_up<<<grid_for((int64_t)N * H * W * (Cx / 8), u->n_sm), 256, 0, st>>>(in0, in1, u->dcat, N, H, W, c.c0,
+                                                                                  c.c1);
+    X = u->dcat;
+  }
+  if (Cx % 8 || c.cout % 32 || c.cin_pad % 8 || Cx > c.cin_pad) return cudaErrorInvalidValue;
+  CUtensorMap tmx, tmy;
+  if (!nhwc_map(&tmx, X, Cx, W, H, N, 18, 10) || !nhwc_map(&tmy, dy, c.cout, W, H, N, 16, 8))
+    return cudaErrorInvalidValue;
   WgradArgs a;
-  a.in0 = in0;
-  a.in1 = in1;
-  a.c0 = c.c0;
-  a.c1 = c.c1;
-  a.up0 = c.up0;
+  a.Cx = Cx;
   a.cin_pad = c.cin_pad;
-  a.dy = dy;
-  a.dw = dw_pad;
   a.cout = c.cout;
+  a.dw = dw_pad;
   a.N = N;
   a.H = H;
   a.W = W;
-  const int64_t P = (int64_t)N * H * W;
-  const int blocks_yz = 9 * (c.cin_pad / 32) * (c.cout / (c.cout % 64 == 0 ? 64 : 32));
-  int64_t splits = ((int64_t)u->n_sm * 8 + blocks_yz - 1) / blocks_yz;
+  a.tiles = N * ((H + 7) / 8) * ((W + 15) / 16);
+  a.err = u->d_err;
+  // output-channel block and tap group: TMEM holds the tap group's accumulators (<= 512 columns)
+  const int NB = c.cout % 128 == 0 ? 128 : (c.cout % 64 == 0 ? 64 : 32);
+  const int TAPG = NB == 128 ? 3 : (NB == 64 ? 5 : 9);
+  const int mbk = (Cx + 127) / 128, groups = (c.cout / NB) * ((9 + TAPG - 1) / TAPG);
+  int splits = (u->n_sm + mbk * groups - 1) / (mbk * groups);  // about one block per SM
+  if (splits > a.tiles / 8) splits = a.tiles / 8;  // at least 8 tiles per block: the epilogue's atomics
+                                                  // cost about as much as 8 tiles of MMAs
   if (splits < 1) splits = 1;
-  int64_t per = (P + splits - 1) / splits;
-  per = (per + 31) / 32 * 32;
-  splits = (P + per - 1) / per;
-  a.pix_per_split = per;
-  if (c.cout % 64 == 0) {
-    dim3 g((unsigned)splits, 9 * (c.cin_pad / 32), c.cout / 64);
-    k_wgrad3x3<64><<<g, 128, 0, st>>>(a);
-  } else {
-    dim3 g((unsigned)splits, 9 * (c.cin_pad / 32), c.cout / 32);
-    k_wgrad3x3<32><<<g, 128, 0, st>>>(a);
+  const dim3 grid((unsigned)splits, (unsigned)mbk, (unsigned)groups);
+  switch (NB) {
+    case 128: launch_wgrad<128, 3, 2>(grid, tmx, tmy, a, st); break;
+    case 64: launch_wgrad<64, 5, 3>(grid, tmx, tmy, a, st); break;
+    default: launch_wgrad<32, 9, 3>(grid, tmx, tmy, a, st); break;
   }
   return cudaGetLastError();
 }
@@ -1072,11 +1187,7 @@ cudaError_t backward(mem_unet* u, int N, int H, int W, cudaStream_t st) {
       k_unpad_rows<<<grid_for(9LL * c.cin * c.cout, u->n_sm), 256, 0, st>>>(u->g0pad, u->grads + c.w_off, c.cin,
                                                                             c.cin_pad, c.cout);
     // bias gradient
-    {
-      const int lanes = 256 / c.cout;
-      k_bias_grad<<<grid_for(Pl / lanes + 1, u->n_sm), lanes * c.cout, 0, st>>>(u->dact[i], u->grads + c.b_off, Pl,
-                                                                                 c.cout);
-    }
+    k_bias_grad<<<u->n_sm * 2, 256, 0, st>>>(u->dact[i], u->grads + c.b_off, Pl, c.cout);
     if (i == 0) break;
     // data gradient into the layer input
     if (c.c1) {  // decoder concat input: d(concat) then split
