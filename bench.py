@@ -501,7 +501,7 @@ def bench_inpaint(args, dev, flush, ws):
             "unet_inference_ms": round(1e3 * t_inf, 3), "unet_inference_crops_per_s": round(ws * B / t_inf, 1),
             "unet_conv_tflops": round(tf, 1), "unet_conv_frac_of_bf16_peak": round(tf / peaks_bf16, 4),
             "unet_train_step_ms_16_crops": round(1e3 * t_train, 3),
-            "note": "3x3 convolutions (forward and data gradient) run on tcgen05 BF16 MMAs with float32 accumulators in tensor memory; the weight gradient on mma.sync"}
+            "note": "3x3 convolutions (forward, data and weight gradients) run on tcgen05 BF16 MMAs with float32 accumulators in tensor memory, operands loaded by TMA"}
 
 
 def bench_image(args, dev, flush, ws, c2):
