@@ -597,64 +597,123 @@ __global__ void k_cat_up(const bf16* __restrict__ in0, const bf16* __restrict__ 
 // added to `acc` (the gradient that reached the same tensor through the skip)
 __global__ void k_maxpool_bwd(const bf16* __restrict__ x, const bf16* __restrict__ dy, bf16* __restrict__ acc,
                               int N, int H, int W, int C) {
-  const int Ho = H / 2, Wo = W / 2;
-  const int64_t total = (int64_t)N * Ho * Wo * C;
+  // a thread owns one 8-channel chunk (16-byte accesses) of one 2x2 window
+  const int Ho = H / 2, Wo = W / 2, chunks = C / 8;
+  const int64_t total = (int64_t)N * Ho * Wo * chunks;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const int c = (int)(i % C);
-    int64_t r = i / C;
+    const int c = (int)(i % chunks) * 8;
+    int64_t r = i / chunks;
     const int xo = (int)(r % Wo);
     r /= Wo;
     const int yo = (int)(r % Ho);
     const int n = (int)(r / Ho);
     const int64_t base = (((int64_t)n * H + 2 * yo) * W + 2 * xo) * C + c;
     const int64_t off[4] = {0, C, (int64_t)W * C, (int64_t)W * C + C};
-    int am = 0;
-    float best = __bfloat162float(x[base]);
-    for (int k = 1; k < 4; ++k) {
-      const float v = __bfloat162float(x[base + off[k]]);
-      if (v > best) {
-        best = v;
-        am = k;
+    float xv[4][8];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const uint4 v = *reinterpret_cast<const uint4*>(x + base + off[k]);
+      const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float2 f = __bfloat1622float2(h[j]);
+        xv[k][2 * j] = f.x;
+        xv[k][2 * j + 1] = f.y;
       }
     }
-    const float g = __bfloat162float(dy[i]);
+    int am[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {  // first maximum of the window in row-major order
+      am[j] = 0;
+      float best = xv[0][j];
+#pragma unroll
+      for (int k = 1; k < 4; ++k)
+        if (xv[k][j] > best) {
+          best = xv[k][j];
+          am[j] = k;
+        }
+    }
+    const uint4 gv = *reinterpret_cast<const uint4*>(dy + i * 8);
+    const __nv_bfloat162* gh = reinterpret_cast<const __nv_bfloat162*>(&gv);
+    float g[8];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float2 f = __bfloat1622float2(gh[j]);
+      g[2 * j] = f.x;
+      g[2 * j + 1] = f.y;
+    }
+#pragma unroll
     for (int k = 0; k < 4; ++k) {
-      const float prev = __bfloat162float(acc[base + off[k]]);
-      acc[base + off[k]] = __float2bfloat16_rn(prev + (k == am ? g : 0.f));
+      uint4* ap = reinterpret_cast<uint4*>(acc + base + off[k]);
+      uint4 v = *ap;
+      __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&v);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float2 f = __bfloat1622float2(h[j]);
+        h[j] = __floats2bfloat162_rn(f.x + (am[2 * j] == k ? g[2 * j] : 0.f), f.y + (am[2 * j + 1] == k ? g[2 * j + 1] : 0.f));
+      }
+      *ap = v;
     }
   }
 }
 
-// ReLU gradient in place: dy *= (y > 0)
+// ReLU gradient in place: dy *= (y > 0), 8 channels (16 bytes) per step
 __global__ void k_relu_bwd(const bf16* __restrict__ y, bf16* __restrict__ dy, int64_t n) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    if (!(__bfloat162float(y[i]) > 0.f)) dy[i] = __float2bfloat16_rn(0.f);
+  const int64_t n8 = n / 8;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n8; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint4 yv = *reinterpret_cast<const uint4*>(y + i * 8);
+    uint4 dv = *reinterpret_cast<const uint4*>(dy + i * 8);
+    const __nv_bfloat162* yh = reinterpret_cast<const __nv_bfloat162*>(&yv);
+    __nv_bfloat162* dh = reinterpret_cast<__nv_bfloat162*>(&dv);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float2 f = __bfloat1622float2(yh[j]);
+      const float2 d = __bfloat1622float2(dh[j]);
+      dh[j] = __floats2bfloat162_rn(f.x > 0.f ? d.x : 0.f, f.y > 0.f ? d.y : 0.f);
+    }
+    *reinterpret_cast<uint4*>(dy + i * 8) = dv;
+  }
 }
 
 // gradient of concat([upsample(low), skip]): low gets the 2x2 sums of the
-// first c_up channels, skip the remaining channels
+// first c_up channels, skip the remaining channels; 8 channels (16 bytes) per step
 __global__ void k_split_cat_bwd(const bf16* __restrict__ dcat, bf16* __restrict__ dlow,
                                 bf16* __restrict__ dskip, int N, int H, int W, int c_up, int c_skip) {
   const int Ho = H / 2, Wo = W / 2;
-  const int C = c_up + c_skip;
-  const int64_t tl = (int64_t)N * Ho * Wo * c_up;
+  const int C = c_up + c_skip, cu8 = c_up / 8, cs8 = c_skip / 8;
+  const int64_t tl = (int64_t)N * Ho * Wo * cu8;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < tl; i += (int64_t)gridDim.x * blockDim.x) {
-    const int c = (int)(i % c_up);
-    int64_t r = i / c_up;
+    const int c = (int)(i % cu8) * 8;
+    int64_t r = i / cu8;
     const int xo = (int)(r % Wo);
     r /= Wo;
     const int yo = (int)(r % Ho);
     const int n = (int)(r / Ho);
     const int64_t b = (((int64_t)n * H + 2 * yo) * W + 2 * xo) * C + c;
-    const float s = __bfloat162float(dcat[b]) + __bfloat162float(dcat[b + C]) +
-                    __bfloat162float(dcat[b + (int64_t)W * C]) + __bfloat162float(dcat[b + (int64_t)W * C + C]);
-    dlow[i] = __float2bfloat16_rn(s);
+    const int64_t off[4] = {0, C, (int64_t)W * C, (int64_t)W * C + C};
+    float s[8];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const uint4 v = *reinterpret_cast<const uint4*>(dcat + b + off[k]);
+      const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float2 f = __bfloat1622float2(h[j]);
+        s[2 * j] = k ? s[2 * j] + f.x : f.x;
+        s[2 * j + 1] = k ? s[2 * j + 1] + f.y : f.y;
+      }
+    }
+    uint4 o;
+    __nv_bfloat162* oh = reinterpret_cast<__nv_bfloat162*>(&o);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) oh[j] = __floats2bfloat162_rn(s[2 * j], s[2 * j + 1]);
+    *reinterpret_cast<uint4*>(dlow + i * 8) = o;
   }
-  const int64_t ts = (int64_t)N * H * W * c_skip;
+  const int64_t ts = (int64_t)N * H * W * cs8;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ts; i += (int64_t)gridDim.x * blockDim.x) {
-    const int c = (int)(i % c_skip);
-    const int64_t p = i / c_skip;
-    dskip[i] = dcat[p * C + c_up + c];
+    const int c = (int)(i % cs8) * 8;
+    const int64_t p = i / cs8;
+    *reinterpret_cast<uint4*>(dskip + i * 8) = *reinterpret_cast<const uint4*>(dcat + p * C + c_up + c);
   }
 }
 
@@ -1175,7 +1234,7 @@ cudaError_t backward(mem_unet* u, int N, int H, int W, cudaStream_t st) {
     const int l = c.level;
     const int Hl = H >> l, Wl = W >> l;
     const int64_t Pl = (int64_t)N * Hl * Wl;
-    k_relu_bwd<<<grid_for(Pl * c.cout, u->n_sm), 256, 0, st>>>(u->act[i], u->dact[i], Pl * c.cout);
+    k_relu_bwd<<<grid_for(Pl * c.cout / 8, u->n_sm), 256, 0, st>>>(u->act[i], u->dact[i], Pl * c.cout);
     const int c0 = i == 0 ? 16 : c.c0;
     ConvLayer cc = c;
     cc.c0 = c0;
@@ -1195,7 +1254,7 @@ cudaError_t backward(mem_unet* u, int N, int H, int W, cudaStream_t st) {
       if (e != cudaSuccess) return e;
       // low-resolution source gradient -> dact of the producing layer; skip -> dact of the skip layer
       const int lowi = i - 1, skipi = (i == 8) ? 5 : (i == 10 ? 3 : 1);
-      k_split_cat_bwd<<<grid_for(Pl * c.cin, u->n_sm), 256, 0, st>>>(u->dcat, u->dact[lowi], u->dact[skipi], N, Hl, Wl,
+      k_split_cat_bwd<<<grid_for(Pl * c.cin / 8, u->n_sm), 256, 0, st>>>(u->dcat, u->dact[lowi], u->dact[skipi], N, Hl, Wl,
                                                                       c.c0, c.c1);
     } else if (i == 2 || i == 4 || i == 6) {  // input is a pooled tensor
       const int lv = i / 2 - 1;
@@ -1205,7 +1264,7 @@ cudaError_t backward(mem_unet* u, int N, int H, int W, cudaStream_t st) {
       // route through the pooling and add to the skip gradient already in dact[i - 1]
       const int src = i - 1;
       const ConvLayer& ps = u->L[src];
-      k_maxpool_bwd<<<grid_for((int64_t)N * Hl * Wl * ps.cout, u->n_sm), 256, 0, st>>>(
+      k_maxpool_bwd<<<grid_for((int64_t)N * Hl * Wl * ps.cout / 8, u->n_sm), 256, 0, st>>>(
           u->act[src], u->dpool[lv], u->dact[src], N, Hl * 2, Wl * 2, ps.cout);
     } else {
       e = conv(u, c, u->dact[i], nullptr, c.wd, nullptr, u->dact[i - 1], c.cin, c.cout_pad, c.cout, 0, 0, N, Hl, Wl,
