@@ -204,8 +204,19 @@ mem_status mem_set_layer(mem_map *m, int32_t map_index, int32_t layer, int32_t p
                          const void *src, void *stream);
 /* World xy of the centre of map `map_index` (host output). */
 mem_status mem_get_origin(const mem_map *m, int32_t map_index, double out_xy[2]);
-/* Synchronise `stream` and report (then clear) the map's device error word. */
+/* Synchronise `stream` and report (then clear) the map's device error word.
+ * While the word is set, the point path's kernels of this map return without
+ * work (the map state is left as it was), so a failed call changes nothing. */
 mem_status mem_check(mem_map *m, void *stream);
+
+/* Fault injection for tests (no GPU fault, trap or hang): with
+ * MEM_FAULT_SORT_WAIT, every wait of the radix sort's look-back treats its
+ * predecessor as not ready, so the bounded wait runs out (a few seconds),
+ * the error word is set and the rest of the call does nothing; mem_check then
+ * returns MEM_ERR_TIMEOUT. MEM_FAULT_NONE restores normal operation.
+ * Synchronises the device. */
+typedef enum { MEM_FAULT_NONE = 0, MEM_FAULT_SORT_WAIT = 1 } mem_fault;
+mem_status mem_inject_fault(mem_map *m, int32_t kind);
 
 /* Schedule of the point path (no effect on the results): radix_bits in
  * [8, 10] is the digit width of the key sort (at most 4 passes);

@@ -445,7 +445,7 @@ extern "C" mem_status mem_create_map(const mem_map_config* cfg, mem_map** out) {
   }
   ALLOC(md.hist, uint32_t, 4 * 1024 + 16, "alloc hist");
   md.counters = md.hist + 4 * 1024;
-  ALLOC(md.err, int, 1, "alloc err");
+  ALLOC(md.err, int, 2, "alloc err");  // [0] error word, [1] fault injection
 #undef ALLOC
   e = alloc_scratch(m, cfg->max_points > 0 ? cfg->max_points : (1 << 20));
   if (e != cudaSuccess) return bail(e, "alloc scratch");
@@ -467,7 +467,7 @@ extern "C" mem_status mem_create_map(const mem_map_config* cfg, mem_map** out) {
   m->key_bits = key_bits_for(m);
   m->tune.radix_bits = m->key_bits <= 16 ? 8 : 9;
   m->passes = (m->key_bits + m->tune.radix_bits - 1) / m->tune.radix_bits;
-  if ((e = cudaMemset(md.err, 0, sizeof(int))) != cudaSuccess) return bail(e, "memset");
+  if ((e = cudaMemset(md.err, 0, 2 * sizeof(int))) != cudaSuccess) return bail(e, "memset");
   if ((e = launch_init_state(m, 0)) != cudaSuccess) return bail(e, "init");
   if ((e = cudaDeviceSynchronize()) != cudaSuccess) return bail(e, "init sync");
   *out = mm;
@@ -1046,6 +1046,16 @@ extern "C" mem_status mem_get_stats(mem_map* mm, void* stream, int64_t out[4]) {
   out[1] = c[5];
   out[2] = c[6];
   out[3] = m->passes;
+  return MEM_OK;
+}
+
+extern "C" mem_status mem_inject_fault(mem_map* mm, int32_t kind) {
+  if (!mm) return fail(MEM_ERR_ARG, "NULL argument");
+  if (kind != MEM_FAULT_NONE && kind != MEM_FAULT_SORT_WAIT) return fail(MEM_ERR_ARG, "unknown fault kind %d", kind);
+  Map* m = &mm->m;
+  CK(cudaDeviceSynchronize(), "synchronize");
+  const int v = kind;
+  CK(cudaMemcpy(m->md.err + 1, &v, sizeof(int), cudaMemcpyHostToDevice), "write fault word");
   return MEM_OK;
 }
 

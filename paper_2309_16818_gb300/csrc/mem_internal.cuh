@@ -67,7 +67,7 @@ struct MapDev {
                     // [6] kept points, [7] [9] tile counters of the fuse kernels, [8] slots
   float* partial;   // fuse scratch: tile slot bases, tile run counts, slots of acc words
   int64_t partial_cap;  // floats
-  int* err;
+  int* err;         // [0] device error word (bounded wait ran out), [1] fault injection for tests
   int64_t cap;      // point capacity of the scratch
   int64_t cap_tiles;
 };

@@ -44,6 +44,7 @@ __global__ void __launch_bounds__(256) k_points_key(MapDev md, const PointJob* _
                                                     int passes) {
   constexpr int RADIX = 1 << RB;
   extern __shared__ u32 shist[];  // [passes][RADIX], then the kept-point count
+  if (*(volatile int*)md.err) return;  // a device error is pending: the point path does nothing
   for (int i = threadIdx.x; i <= passes * RADIX; i += blockDim.x) shist[i] = 0;
   __syncthreads();
   const int64_t n = job->n;
@@ -142,7 +143,14 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(MapDev md, const Poin
   u32* sgdig = (u32*)(sgbase + RADIX);   // [RADIX] exclusive offsets of the digits over all keys
   __shared__ int s_tile;
   __shared__ u32 s_wsum[WARPS];
+  __shared__ volatile int s_fail;  // a look-back wait of this tile ran out: no scatter
 
+  // a device error is pending (the word can be set by other blocks of this pass meanwhile, so the
+  // block decides once, through shared memory): the point path does nothing
+  if (threadIdx.x == 0) s_fail = *(volatile int*)md.err;
+  __syncthreads();
+  if (s_fail) return;
+  const bool inject = *(volatile int*)(md.err + 1) != 0;  // fault injection (tests): waits run out
   const int64_t n = job->n;
   const int n_tiles = (int)((n + kTile - 1) / kTile);
   const int shift = pass * RB;
@@ -262,6 +270,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(MapDev md, const Poin
         // an inclusive prefix is found; wait (bounded) where one is not ready
         int k = tile - 1;
         u32 spins = 0;
+        bool timed_out = false;
         for (;;) {
           u32 v[kLookBack];
 #pragma unroll
@@ -272,7 +281,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(MapDev md, const Poin
 #pragma unroll
           for (int j = 0; j < kLookBack; ++j) {
             if (!fin && !wait) {
-              const u32 f = v[j] & kLbFlags;
+              const u32 f = inject ? 0u : (v[j] & kLbFlags);
               if (f == 0) {
                 wait = true;
                 adv = j;
@@ -285,18 +294,22 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(MapDev md, const Poin
           if (fin) break;
           k -= adv;
           if (wait) {
-            if (++spins > kSpinLimit) {
+            if (++spins > kSpinLimit || s_fail) {
               atomicExch(md.err, kDevErrTimeout);
+              s_fail = 1;
+              timed_out = true;
               break;
             }
             __nanosleep(32);
           }
         }
-        st_relaxed(me, kLbP | ((excl + c) & kLbVal));
+        // a tile whose wait ran out keeps its aggregate flag: successors still reach a correct prefix
+        if (!timed_out) st_relaxed(me, kLbP | ((excl + c) & kLbVal));
       }
       sgbase[d] = (int)(sgdig[d] + excl) - sstart[d];
     }
     __syncthreads();
+    if (s_fail) break;  // the prefixes are unknown: write nothing (the error word is set)
     // stage the tile in digit order, then write runs of equal digits
 #pragma unroll
     for (int j = 0; j < kSortItems; ++j) {
@@ -733,6 +746,7 @@ __global__ void __launch_bounds__(kFT, 6) k_fuse_tiles(MapDev md, const PointJob
                                                        int sorted1) {
   extern __shared__ __align__(16) unsigned char fz_raw[];
   SumSmem& s = *reinterpret_cast<SumSmem*>(fz_raw);
+  if (*(volatile int*)md.err) return;  // a device error is pending: the point path does nothing
   const u32* __restrict__ sk = sorted1 ? md.keys1 : md.keys0;
   const u32* __restrict__ sv = sorted1 ? md.vals1 : md.vals0;
   const int64_t n_kept = *(volatile u32*)&md.counters[6];
@@ -1083,6 +1097,7 @@ __global__ void __launch_bounds__(kFT, 6) k_fuse_tiles(MapDev md, const PointJob
 // column over the pieces in tile order and loads the old values of the
 // column's layers together, then stores the new values.
 __global__ void __launch_bounds__(128) k_fuse_cross(MapDev md, const PointJob* __restrict__ job) {
+  if (*(volatile int*)md.err) return;  // a device error is pending: the point path does nothing
   __shared__ LayerDev sL[kMaxLayers];
   __shared__ SrcDev ssrc[kMaxSources];
   __shared__ int srlay[kMaxSources][kMaxSrcLayers], snrlay[kMaxSources];
@@ -1220,6 +1235,7 @@ __global__ void __launch_bounds__(128) k_fuse_cross(MapDev md, const PointJob* _
 
 // time-dependent variance growth of every valid cell
 __global__ void k_time_update(MapDev md, int64_t cells) {
+  if (*(volatile int*)md.err) return;  // a device error is pending: the point path does nothing
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < cells;
        g += (int64_t)gridDim.x * blockDim.x)
     if (md.flags[g] & kFlagValid) md.var[g] = __fadd_rn(md.var[g], md.time_var);

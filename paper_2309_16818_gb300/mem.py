@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(HERE, "libmem.so")
 
 MAX_LAYERS, MAX_SOURCES, MAX_SOURCE_LAYERS = 16, 8, 8
 OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_TIMEOUT, ERR_STATE = range(6)
+FAULT_NONE, FAULT_SORT_WAIT = 0, 1
 LATEST, EXPAVG, GAUSS, DIRICHLET, CLASSMAX = range(5)
 F32, BF16, F16, U8 = range(4)
 LAYER_HEIGHT, LAYER_VARIANCE, LAYER_VALID, LAYER_NACC, LAYER_NREJ = -1, -2, -3, -4, -5
@@ -29,7 +30,7 @@ EXPORTS = ["mem_create_map", "mem_destroy_map", "mem_move_map", "mem_fuse_pointc
            "mem_set_profiling", "mem_get_profile", "mem_get_stats", "mem_fuse_pointcloud_noalloc",
            "mem_autotune_batch", "mem_inpaint_diffusion", "mem_unet_create", "mem_unet_destroy",
            "mem_unet_param_count", "mem_unet_set_params", "mem_unet_get_params", "mem_unet_forward",
-           "mem_unet_gradients", "mem_unet_train_step", "mem_unet_check"]
+           "mem_unet_gradients", "mem_unet_train_step", "mem_unet_check", "mem_inject_fault"]
 NOALLOC_MAX_POINTS = 1 << 18
 PROFILE_SLOTS = ["key", "digit_scan", "radix_sort", "unused3", "fuse_tiles", "fuse_cross",
                  "time_var", "image", "move"]
@@ -90,7 +91,7 @@ def lib():
             "mem_unet_forward": [P, I32, I32, I32, P, P, P, P],
             "mem_unet_gradients": [P, I32, I32, I32, P, P, P, P, I64, P, P, P],
             "mem_unet_train_step": [P, I32, I32, I32, P, P, P, P, I64, C.c_float, P, P],
-            "mem_unet_check": [P, P],
+            "mem_unet_check": [P, P], "mem_inject_fault": [P, I32],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -313,6 +314,10 @@ class Map:
 
     def check(self, stream=None):
         _ck(lib().mem_check(self._h, _stream(stream)))
+
+    def inject_fault(self, kind):
+        """Tests only: FAULT_SORT_WAIT makes the sort's bounded waits run out; FAULT_NONE clears."""
+        _ck(lib().mem_inject_fault(self._h, kind))
 
     def set_tuning(self, radix_bits, blocks_per_sm):
         _ck(lib().mem_set_tuning(self._h, radix_bits, blocks_per_sm))

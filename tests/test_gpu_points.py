@@ -262,3 +262,38 @@ def test_host_buffer_fuse_equals_device_fuse(torch):
         a = dev.get_layer(lay).cpu().numpy()
         b = host.get_layer(lay).cpu().numpy()
         assert np.array_equal(a.view(np.uint8), b.view(np.uint8)), lay
+
+
+def test_injected_sort_wait_timeout_reports_and_changes_nothing(torch):
+    """Fault injection from the host: the radix sort's look-back waits are made to run out. The
+    call must come back (bounded waits, no trap, no hang), mem_check must report MEM_ERR_TIMEOUT,
+    the map must be left exactly as before the call, and after the fault is cleared the same call
+    must give the oracle's result."""
+    import time
+    from paper_2309_16818_gb300 import mem as M
+    c = synth.config1()
+    cl = c["cloud"]
+    layers = [dict(channels=3, rule=O.LATEST)]
+    g, o = make_pair(c["W"], c["res"], layers)
+    src = [(torch.from_numpy(cl.rgb).cuda(), [0])]
+    o.fuse_points(cl.xyz, cl.T, [(cl.rgb, [0])])
+    g.fuse_pointcloud(cuda_xyz(cl), cl.T, src)
+    g.check()
+    before = gpu_state(g)
+    g.inject_fault(M.FAULT_SORT_WAIT)
+    t0 = time.time()
+    g.fuse_pointcloud(cuda_xyz(cl), cl.T, src)
+    with pytest.raises(M.MemError) as e:
+        g.check()
+    assert e.value.status == M.ERR_TIMEOUT
+    assert time.time() - t0 < 60
+    after = gpu_state(g)
+    for k in ("h", "var", "valid", "n_acc", "n_rej"):
+        assert np.array_equal(after[k], before[k]), k
+    assert np.array_equal(after["layers"][0], before["layers"][0])
+    g.inject_fault(M.FAULT_NONE)
+    g.check()  # the error word was cleared by the failed check
+    o.fuse_points(cl.xyz, cl.T, [(cl.rgb, [0])])
+    g.fuse_pointcloud(cuda_xyz(cl), cl.T, src)
+    g.check()
+    compare_states(gpu_state(g), o, what="after the injected fault")
