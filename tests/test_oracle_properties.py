@@ -1,0 +1,131 @@
+"""Property tests of the oracle over random small inputs (hypothesis): permutation invariance of a
+call's result (Sec. III-B/III-C define per-cell sums, so the order of points cannot matter beyond
+floating-point reassociation), the Dirichlet update adds exactly the per-cell probability sums
+(Eq. 12) and its posterior mean sums to one, the class max is the per-cell arg-max with the
+smallest index on ties, the height of a fresh cell is the precision-weighted mean of its readings
+with variance 1 / sum of precisions, and a move commutes with a fuse on the cells both frames
+share. CPU only."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+hyp = pytest.importorskip("hypothesis")
+from hypothesis import given, settings  # noqa: E402
+from hypothesis import strategies as st  # noqa: E402
+
+SETTINGS = dict(max_examples=25, deadline=None, derandomize=True)
+
+
+def ident():
+    return np.eye(4)
+
+
+def cloud(seed, n, W, res, k):
+    rng = np.random.default_rng(seed)
+    half = W * res / 2
+    pts = np.column_stack([rng.uniform(-half + 1e-3, half - 1e-3, size=(n, 2)),
+                           rng.normal(-1.0, 0.05, size=n)]).astype(np.float32)
+    p = rng.random((n, k)).astype(np.float32) + np.float32(0.01)
+    probs = (p / p.sum(axis=1, keepdims=True)).astype(np.float32)
+    rgb = rng.integers(0, 256, size=(n, 3), dtype=np.uint8)
+    return rng, pts, probs, rgb
+
+
+def groups(cells):
+    g = {}
+    for i, c in enumerate(cells):
+        if c >= 0:
+            g.setdefault(int(c), []).append(i)
+    return g
+
+
+@settings(**SETTINGS)
+@given(seed=st.integers(0, 2 ** 31 - 1), n=st.integers(1, 300), k=st.integers(2, 6))
+def test_result_does_not_depend_on_point_order(seed, n, k):
+    rng, pts, probs, rgb = cloud(seed, n, 8, 0.5, k)
+    L = [O.Layer(3, O.LATEST), O.Layer(k, O.DIRICHLET), O.Layer(k, O.CLASSMAX), O.Layer(k, O.EXPAVG, w=0.3),
+         O.Layer(k, O.GAUSS, var_meas=0.5)]
+    perm = rng.permutation(n)
+    maps = []
+    for order in (np.arange(n), perm):
+        m = O.OracleMap(O.Params(W=8, res=0.5, layers=L), round_store=False)
+        for _ in range(2):
+            m.fuse_points(pts[order], ident(), [(rgb[order], [0]), (probs[order], [1, 2, 3, 4])])
+        maps.append(m)
+    a, b = maps
+    np.testing.assert_array_equal(a.valid, b.valid)
+    np.testing.assert_array_equal(a.n_acc, b.n_acc)
+    np.testing.assert_array_equal(a.n_rej, b.n_rej)
+    np.testing.assert_allclose(a.h, b.h, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(a.var, b.var, rtol=1e-12, atol=0)
+    for l in range(len(L)):
+        np.testing.assert_allclose(a.layer[l], b.layer[l], rtol=1e-12, atol=1e-12)
+
+
+@settings(**SETTINGS)
+@given(seed=st.integers(0, 2 ** 31 - 1), n=st.integers(1, 200), k=st.integers(2, 8),
+       alpha0=st.sampled_from([0.5, 1.0, 2.0]))
+def test_dirichlet_adds_probability_sums_and_class_max_is_the_argmax(seed, n, k, alpha0):
+    _, pts, probs, _ = cloud(seed, n, 8, 0.5, k)
+    L = [O.Layer(k, O.DIRICHLET, alpha0=alpha0), O.Layer(k, O.CLASSMAX)]
+    m = O.OracleMap(O.Params(W=8, res=0.5, layers=L), round_store=False)
+    r = m.fuse_points(pts, ident(), [(probs, [0, 1])], want_cells=True)
+    g = groups(r["cells"])
+    alpha = m.layer_values(0)
+    cm = m.layer_values(1)
+    for c, idx in g.items():
+        s = probs[idx].astype(np.float64).sum(axis=0)
+        np.testing.assert_allclose(alpha[c], alpha0 + s, rtol=1e-12)
+        assert math.isclose(float(m.theta(0)[c].sum()), 1.0, rel_tol=1e-12)
+        mx = probs[idx].astype(np.float64).max(axis=0)
+        best = int(np.flatnonzero(mx == mx.max())[0])  # smallest class index among the maxima
+        assert int(cm[c, 0]) == best and cm[c, 1] == mx.max()
+    untouched = np.setdiff1d(np.arange(64), list(g))
+    assert np.all(m.obs[0][untouched] == 0) and np.all(alpha[untouched] == alpha0)
+
+
+@settings(**SETTINGS)
+@given(seed=st.integers(0, 2 ** 31 - 1), n=st.integers(1, 120))
+def test_fresh_cell_height_is_the_precision_weighted_mean(seed, n):
+    """Identity pose (the transform is exact), gate off: per cell h = sum(z / s^2) / sum(1 / s^2)
+    and var = 1 / sum(1 / s^2), s = sigma0 + sigma1 * range (range and s rounded to float32 by the
+    oracle, so the closed form is taken at 1e-6)."""
+    _, pts, _, _ = cloud(seed, n, 8, 0.5, 2)
+    p = O.Params(W=8, res=0.5, gate_lambda=1e6)
+    m = O.OracleMap(p, round_store=False)
+    r = m.fuse_points(pts, ident(), want_cells=True)
+    x = pts.astype(np.float64)
+    rng_ = np.sqrt((x ** 2).sum(axis=1))
+    s = p.sigma0 + p.sigma1 * rng_
+    w = 1.0 / (s * s)
+    for c, idx in groups(r["cells"]).items():
+        sw = w[idx].sum()
+        assert m.var[c] == pytest.approx(1.0 / sw, rel=1e-6)
+        assert m.h[c] == pytest.approx((w[idx] * x[idx, 2]).sum() / sw, rel=1e-6, abs=1e-6)
+        assert m.n_acc[c] == len(idx) and m.valid[c] == 1
+
+
+@settings(**SETTINGS)
+@given(seed=st.integers(0, 2 ** 31 - 1), n=st.integers(1, 200), sx=st.integers(-3, 3), sy=st.integers(-3, 3))
+def test_move_commutes_with_fuse_on_shared_cells(seed, n, sx, sy):
+    W, res = 12, 0.5
+    _, pts, probs, rgb = cloud(seed, n, W, res, 3)
+    L = [O.Layer(3, O.LATEST), O.Layer(3, O.DIRICHLET)]
+    xy = (sx * res, sy * res)
+    T = ident()
+    a = O.OracleMap(O.Params(W=W, res=res, layers=L, gate_lambda=1e6))
+    a.fuse_points(pts, T, [(rgb, [0]), (probs, [1])])
+    a.move(xy)
+    b = O.OracleMap(O.Params(W=W, res=res, layers=L, gate_lambda=1e6))
+    b.move(xy)
+    b.fuse_points(pts, T, [(rgb, [0]), (probs, [1])])
+    # new cell (ix, iy) was old (ix + sx, iy + sy): compare where that old cell existed
+    ys, xs = np.mgrid[0:W, 0:W]
+    keep = ((xs + sx >= 0) & (xs + sx < W) & (ys + sy >= 0) & (ys + sy < W)).ravel()
+    assert np.array_equal(a.valid[keep], b.valid[keep])
+    np.testing.assert_array_equal(a.h[keep], b.h[keep])
+    np.testing.assert_array_equal(a.layer_values(0)[keep], b.layer_values(0)[keep])
+    np.testing.assert_array_equal(a.layer_values(1)[keep], b.layer_values(1)[keep])
