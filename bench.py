@@ -171,22 +171,31 @@ def dist_setup():
     return rank, ws, local
 
 
-def barrier(ws):
-    import torch
-    torch.cuda.synchronize()
+def barrier(ws, sync_device=True):
+    """Device synchronise (optional), then a barrier over all ranks."""
+    if sync_device:
+        import torch
+        torch.cuda.synchronize()
     if ws > 1:
         import torch.distributed as dist
         dist.barrier()
 
 
-def max_over_ranks(x: float, ws: int) -> float:
+def max_over_ranks(x: float, ws: int, device="cuda") -> float:
+    """The largest value of x over all ranks (timings: the slowest rank sets the job's time)."""
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, ws: int, seconds_max: float) -> float:
+    """Throughput of the whole job: every rank processes units_per_rank (weak scaling) and the
+    job takes as long as its slowest rank."""
+    return units_per_rank * ws / seconds_max
 
 
 # ----------------------------------------------------------------------------- our arm
@@ -255,7 +264,7 @@ def run_ours(args):
     dev_s = sum(step_ms) / 1e3
     dev_s_max = max_over_ranks(dev_s, ws)
     total_pts = pts * ws
-    value = total_pts / dev_s_max
+    value = whole_job_rate(pts, ws, dev_s_max)
 
     # ---- dominant kernel roofline
     K = args.steps
