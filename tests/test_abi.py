@@ -62,3 +62,52 @@ def test_argument_errors_need_no_device():
     cfg.W, cfg.res = 8, -1.0
     assert mem.lib().mem_create_map(C.byref(cfg), C.byref(h)) == mem.ERR_ARG
     assert mem.lib().mem_fuse_pointcloud(None, 0, None, 0, None, None, None) == mem.ERR_ARG
+
+
+_NULL_PROBE = r'''
+import ctypes as C, sys
+sys.path.insert(0, ROOT)
+from paper_2309_16818_gb300 import mem as M
+L = M.lib()
+for name in M.EXPORTS:
+    if name == "mem_last_error":
+        continue
+    f = getattr(L, name)
+    args = [None if t is C.c_void_p else (1.0 if t is C.c_float else 1) for t in f.argtypes]
+    r = f(*args)
+    print(name, r, bool(L.mem_last_error()))
+w = (C.c_int32 * 4)(32, 64, 128, 128)
+h = C.c_void_p()
+print("unet_cin0", L.mem_unet_create(0, w, C.byref(h)))
+w2 = (C.c_int32 * 4)(32, 48, 128, 128)
+print("unet_width48", L.mem_unet_create(3, w2, C.byref(h)))
+'''
+
+
+def test_null_and_range_arguments_are_rejected_on_the_host():
+    """Every entry point given NULL handles/pointers returns MEM_ERR_ARG with a message (the
+    destroy calls accept NULL like free), and U-Net shape errors are caught before any device
+    work -- all on a machine without a GPU, in a child process so a crash cannot hide."""
+    import subprocess
+    import sys
+    from paper_2309_16818_gb300 import build
+    build.build()
+    r = subprocess.run([sys.executable, "-c", f"ROOT = {ROOT!r}\n" + _NULL_PROBE], capture_output=True, text=True,
+                       timeout=120)
+    assert r.returncode == 0, r.stderr[-2000:]
+    got = {}
+    for line in r.stdout.split("\n"):
+        parts = line.split()
+        if len(parts) >= 2:
+            got[parts[0]] = parts[1:]
+    from paper_2309_16818_gb300 import mem
+    for name in mem.EXPORTS:
+        if name == "mem_last_error":
+            continue
+        status, has_msg = got[name]
+        if name in ("mem_destroy_map", "mem_unet_destroy"):
+            assert status == "0", name
+        else:
+            assert status == str(mem.ERR_ARG) and has_msg == "True", (name, status)
+    assert got["unet_cin0"] == [str(mem.ERR_ARG)]
+    assert got["unet_width48"] == [str(mem.ERR_ARG)]
