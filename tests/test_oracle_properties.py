@@ -129,3 +129,68 @@ def test_move_commutes_with_fuse_on_shared_cells(seed, n, sx, sy):
     np.testing.assert_array_equal(a.h[keep], b.h[keep])
     np.testing.assert_array_equal(a.layer_values(0)[keep], b.layer_values(0)[keep])
     np.testing.assert_array_equal(a.layer_values(1)[keep], b.layer_values(1)[keep])
+
+
+# --------------------------------------------------------------------------- image visibility
+
+def _flat(W, res, height=0.0):
+    m = O.OracleMap(O.Params(W=W, res=res, range_max=1e6, gate_lambda=1e6))
+    xs = (np.arange(W) - W // 2 + 0.5) * res
+    X, Y = np.meshgrid(xs, xs)
+    pts = np.column_stack([X.ravel(), Y.ravel(), np.full(W * W, height - 100.0)]).astype(np.float32)
+    T = np.eye(4)
+    T[2, 3] = 100.0
+    m.fuse_points(pts, T)
+    return m
+
+
+DOWN = np.array([[1.0, 0, 0], [0, -1.0, 0], [0, 0, -1.0]])  # optical axis = world -z
+
+
+@settings(**SETTINGS)
+@given(cx=st.integers(2, 21), cy=st.integers(2, 21), hc=st.floats(1.0, 3.0), pick=st.integers(0, 10 ** 6),
+       pick_q=st.integers(0, 10 ** 6))
+def test_an_occluder_on_the_walk_hides_the_cell_and_removing_it_restores_it(cx, cy, hc, pick, pick_q):
+    """Visibility (Sec. III-B): a cell is seen iff every valid cell strictly between it and the
+    camera's cell on the Bresenham walk lies below the ray. Raising one such cell above the
+    camera hides the target; lowering it again shows it."""
+    W, res = 24, 0.25
+    m = _flat(W, res)
+    pos = ((cx - W // 2 + 0.5) * res, (cy - W // 2 + 0.5) * res, hc)
+    T = np.eye(4)
+    T[:3, :3] = DOWN
+    T[:3, 3] = pos
+    K = (30.0, 30.0, 100.0, 100.0)
+    out = m.fuse_image(200, 200, [], K, T)
+    far = [j for j in np.flatnonzero(out["vis"]) if max(abs(j % W - cx), abs(j // W - cy)) >= 2]
+    if not far:
+        return
+    j = far[pick % len(far)]
+    path = O.bresenham(cx, cy, int(j % W), int(j // W))
+    inner = path[1:-1]
+    q = inner[pick_q % len(inner)]
+    qi = int(q[1]) * W + int(q[0])
+    m.h[qi] = hc + 1.0
+    assert m.fuse_image(200, 200, [], K, T)["vis"][j] == 0
+    m.h[qi] = 0.0
+    assert m.fuse_image(200, 200, [], K, T)["vis"][j] == 1
+
+
+@settings(**SETTINGS)
+@given(seed=st.integers(0, 2 ** 31 - 1), cx=st.integers(0, 23), cy=st.integers(0, 23))
+def test_lowering_other_cells_never_hides_a_visible_cell(seed, cx, cy):
+    W, res = 24, 0.25
+    rng = np.random.default_rng(seed)
+    m = _flat(W, res)
+    m.h[:] = rng.uniform(0.0, 0.6, size=W * W)
+    T = np.eye(4)
+    T[:3, :3] = DOWN
+    T[:3, 3] = ((cx - W // 2 + 0.5) * res, (cy - W // 2 + 0.5) * res, 1.5)
+    K = (30.0, 30.0, 100.0, 100.0)
+    before = m.fuse_image(200, 200, [], K, T)
+    lowered = rng.random(W * W) < 0.5
+    m.h[lowered] -= rng.uniform(0.0, 0.5, size=int(lowered.sum()))
+    after = m.fuse_image(200, 200, [], K, T)
+    same = ~lowered  # cells whose own height (so projection and ray) did not change
+    assert np.all(after["vis"][same] >= before["vis"][same])
+    assert np.array_equal(after["pix"][same & (before["vis"] == 1)], before["pix"][same & (before["vis"] == 1)])
