@@ -111,3 +111,32 @@ def test_null_and_range_arguments_are_rejected_on_the_host():
             assert status == str(mem.ERR_ARG) and has_msg == "True", (name, status)
     assert got["unet_cin0"] == [str(mem.ERR_ARG)]
     assert got["unet_width48"] == [str(mem.ERR_ARG)]
+
+
+@pytest.mark.parametrize("field,value,msg", [
+    ("W", 99, "W must be even"), ("W", 0, "W must be even"), ("res", -1.0, "res must be > 0"),
+    ("n_maps", 0, "n_maps must be >= 1"), ("n_layers", 17, "n_layers out of range"),
+    ("L0_channels", 0, "channels in"), ("L0_rule", 9, "bad rule"), ("L0_dtype", 7, "storage must be"),
+    ("range_min", 5.0, "range_min > range_max"), ("L0_w", 1.5, "w in (0, 1]"),
+    ("L0_dtype", 1, "CLASSMAX / DIRICHLET layers are F32")])
+def test_map_config_is_validated_on_the_host(field, value, msg):
+    """mem_create_map rejects an invalid configuration with MEM_ERR_ARG and a message before any
+    device call (runs without a GPU)."""
+    from paper_2309_16818_gb300 import build, mem
+    build.build()
+    L = mem.lib()
+    c = mem.MapConfig()
+    c.W, c.n_maps, c.res, c.n_layers = 100, 1, 0.05, 1
+    c.layers[0].channels, c.layers[0].dtype = 3, 0
+    c.layers[0].rule = 4 if msg.startswith("CLASSMAX") else (1 if field == "L0_w" else 0)
+    c.layers[0].w, c.layers[0].var_meas, c.layers[0].alpha0 = 0.1, 1.0, 1.0
+    c.sigma0, c.sigma1, c.gate_lambda = 0.01, 0.002, 2.0
+    c.range_min, c.range_max, c.z_near, c.max_points = 0.1, 50.0, 0.05, 1000
+    if field.startswith("L0_"):
+        setattr(c.layers[0], field[3:], value)
+    else:
+        setattr(c, field, value)
+    h = C.c_void_p()
+    assert L.mem_create_map(C.byref(c), C.byref(h)) == mem.ERR_ARG
+    assert msg in L.mem_last_error().decode()
+    assert not h.value
