@@ -117,7 +117,7 @@ def test_null_and_range_arguments_are_rejected_on_the_host():
     ("W", 99, "W must be even"), ("W", 0, "W must be even"), ("res", -1.0, "res must be > 0"),
     ("n_maps", 0, "n_maps must be >= 1"), ("n_layers", 17, "n_layers out of range"),
     ("L0_channels", 0, "channels in"), ("L0_rule", 9, "bad rule"), ("L0_dtype", 7, "storage must be"),
-    ("range_min", 5.0, "range_min > range_max"), ("L0_w", 1.5, "w in (0, 1]"),
+    ("range_min", 60.0, "range_min > range_max"), ("L0_w", 1.5, "w in (0, 1]"),
     ("L0_dtype", 1, "CLASSMAX / DIRICHLET layers are F32")])
 def test_map_config_is_validated_on_the_host(field, value, msg):
     """mem_create_map rejects an invalid configuration with MEM_ERR_ARG and a message before any
