@@ -194,3 +194,26 @@ def test_lowering_other_cells_never_hides_a_visible_cell(seed, cx, cy):
     same = ~lowered  # cells whose own height (so projection and ray) did not change
     assert np.all(after["vis"][same] >= before["vis"][same])
     assert np.array_equal(after["pix"][same & (before["vis"] == 1)], before["pix"][same & (before["vis"] == 1)])
+
+
+@settings(**SETTINGS)
+@given(seed=st.integers(0, 2 ** 31 - 1), n1=st.integers(1, 150), n2=st.integers(1, 150),
+       var_meas=st.sampled_from([0.1, 0.5, 2.0]))
+def test_gaussian_rule_sequential_equals_batch(seed, n1, n2, var_meas):
+    """The Gaussian feature update (Eqs. 6-7) is the conjugate update with known variance, so two
+    calls in a row give the posterior of one call with both sets of points (and the Dirichlet
+    counts add the same way)."""
+    _, pts, probs, _ = cloud(seed, n1 + n2, 8, 0.5, 3)
+    rng = np.random.default_rng(seed + 1)
+    feat = rng.normal(0.0, 1.0, size=(n1 + n2, 3)).astype(np.float32)
+    L = [O.Layer(3, O.GAUSS, var_meas=var_meas), O.Layer(3, O.DIRICHLET)]
+    a = O.OracleMap(O.Params(W=8, res=0.5, layers=L), round_store=False)
+    a.fuse_points(pts[:n1], ident(), [(feat[:n1], [0]), (probs[:n1], [1])])
+    a.fuse_points(pts[n1:], ident(), [(feat[n1:], [0]), (probs[n1:], [1])])
+    b = O.OracleMap(O.Params(W=8, res=0.5, layers=L), round_store=False)
+    b.fuse_points(pts, ident(), [(feat, [0]), (probs, [1])])
+    np.testing.assert_array_equal(a.obs[0], b.obs[0])
+    seen = a.obs[0] == 1
+    np.testing.assert_allclose(a.layer_values(0)[seen], b.layer_values(0)[seen], rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(a.gauss_var(0)[seen], b.gauss_var(0)[seen], rtol=1e-9)
+    np.testing.assert_allclose(a.layer_values(1), b.layer_values(1), rtol=1e-12)
