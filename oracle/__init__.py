@@ -16,7 +16,8 @@ Parity status of each function (what pins it in ``tests/test_oracle_*.py``):
 * ``harmonic_fill`` linear fields and constants reproduced, maximum principle
 
 ``tests/test_oracle_mutants.py`` builds copies of this oracle (and of ``unet.py``) with one
-planted mistake each -- a dropped term, a wrong sign, a transposed index, swapped weights -- and
+planted mistake each -- a dropped term, a wrong sign, a transposed index, swapped weights, an
+off-by-one limit -- and
 requires the pins above to fail on every one. ``tests/golden/make_golden.py`` writes the stored
 expected values of ``tests/golden/fusion_w12.json`` from this oracle alone.
 """

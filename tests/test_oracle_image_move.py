@@ -260,3 +260,17 @@ def test_exact_harmonic_fill_pins():
     h0 = np.arange(64, dtype=float).reshape(8, 8)
     out = O.harmonic_fill_exact(h0, kn)
     np.testing.assert_allclose(out[kn], h0[kn])
+
+
+@pytest.mark.parametrize("above,seen", [(0.04, 0), (0.06, 1)])
+def test_near_plane_is_strict(above, seen):
+    """A cell is projected only when it lies more than z_near (0.05 m) in front of the camera."""
+    W, res = 16, 0.25
+    m = flat_map(W, res, height=0.5)
+    j = 5 * W + 9
+    xc = (9 - W // 2 + 0.5) * res
+    yc = (5 - W // 2 + 0.5) * res
+    out = m.fuse_image(240, 400, [], (300.0, 300.0, 200.0, 120.0), cam_pose(DOWN, (xc, yc, 0.5 + above)))
+    assert out["vis"][j] == seen
+    if seen:
+        assert out["pix"][j] == 120 * 400 + 200

@@ -44,6 +44,26 @@ MUTANTS = {
     "pixel index transposed": [("int64_t p = (int64_t)py * Wi + px;", "int64_t p = (int64_t)px * H + py;")],
     "visibility test not strict": [("if ((float)h0[q] >= ray) {", "if ((float)h0[q] > ray + 1.0f) {")],
     "map move shifts the wrong way": [("long oy = iy + sy;", "long oy = iy - sy;")],
+    "outlier variance without the rejected count":
+        [("s->var[j] + (double)c->outlier_var * nr[j]", "s->var[j] + (double)c->outlier_var")],
+    "time variance added to never-observed cells":
+        [("if (s->valid[j]) s->var[j] = store_round(c, ORC_F32, s->var[j] + (double)c->time_var);",
+          "s->var[j] = store_round(c, ORC_F32, s->var[j] + (double)c->time_var);")],
+    "exponential average blends a never-observed cell":
+        [("double t = s->obs[l][j] ? c->w[l] * a + (1.0 - c->w[l]) * th[j * C + k] : a;",
+          "double t = c->w[l] * a + (1.0 - c->w[l]) * th[j * C + k];")],
+    "Gaussian first observation ignores the count": [("s2 = sf2 / N;", "s2 = sf2;")],
+    "bf16 storage truncates": [("u = (u + 0x7fffu + ((u >> 16) & 1u)) & 0xffff0000u;", "u = u & 0xffff0000u;")],
+    "Dirichlet prior fixed to 1":
+        [("if (c->rule[l] == ORC_DIRICHLET) v = store_round(c, c->store[l], c->alpha0[l]);",
+          "if (c->rule[l] == ORC_DIRICHLET) v = store_round(c, c->store[l], 1.0);")],
+    "class max ties to the largest class": [("if (M[k] > best) {", "if (M[k] >= best) {")],
+    "near plane not applied": [("if (!(Zc > c->z_near)) continue;", "if (!(Zc >= 0.0f)) continue;")],
+    "range filter halves the maximum range":
+        [("if (!(rs >= c->range_min && rs <= c->range_max)) return 0;",
+          "if (!(rs >= c->range_min && rs < c->range_max * 0.5f)) return 0;")],
+    "map edge off by one": [("if (!(qx >= -half && qx < half && qy >= -half && qy < half)) return 0;",
+                             "if (!(qx >= -half && qx <= half && qy >= -half && qy < half)) return 0;")],
 }
 
 

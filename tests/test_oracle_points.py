@@ -367,3 +367,38 @@ def test_bf16_storage_rounding():
     v = np.array([[1.0 + 2 ** -8, 1.0 + 3 * 2 ** -8]], np.float32)  # both ties -> even
     m.fuse_points(q, ident(), [(v, [0])])
     assert list(m.layer_values(0)[36]) == [1.0, 1.0 + 2 ** -6]
+
+
+def test_time_variance_ages_only_valid_cells():
+    """time_var inflates the variance of every valid cell once per call (Sec. III-B reading);
+    cells never observed stay at zero variance and invalid."""
+    p = mk(W=8, res=0.5, time_var=0.25)
+    m = O.OracleMap(p, round_store=False)
+    for _ in range(3):
+        m.fuse_points(np.array([[0.2, 0.2, -1.0]] * 3, np.float32), ident((0, 0, 1.0)))
+    assert m.valid.sum() == 1
+    assert np.all(m.var[m.valid == 0] == 0) and np.all(m.h[m.valid == 0] == 0)
+
+
+def test_classmax_ties_take_the_smallest_class():
+    p = mk(W=8, res=0.5, layers=[O.Layer(4, O.CLASSMAX)])
+    m = O.OracleMap(p, round_store=False)
+    a = np.float32(0.3)
+    pts = np.array([[0.2, 0.2, -1.0], [1.2, 1.2, -1.0], [1.3, 1.3, -1.0]], np.float32)
+    pr = np.array([[a, a, a, np.float32(0.1)],         # one point, three equal maxima
+                   [0.6, 0.4, 0.0, 0.0], [0.4, 0.6, 0.0, 0.0]], np.float32)  # equal maxima across points
+    r = m.fuse_points(pts, ident(), [(pr, [0])], want_cells=True)
+    c0, c1 = int(r["cells"][0]), int(r["cells"][1])
+    assert r["cells"][1] == r["cells"][2]
+    assert m.layer_values(0)[c0][0] == 0 and m.layer_values(0)[c0][1] == pytest.approx(float(a))
+    assert m.layer_values(0)[c1][0] == 0 and m.layer_values(0)[c1][1] == pytest.approx(0.6)
+
+
+def test_range_limits_are_inclusive():
+    """A point is kept iff range_min <= |p_s| <= range_max (Sec. III-B filter); points on the
+    optical axis have exactly representable ranges here."""
+    p = mk(W=8, res=0.5, range_min=0.5, range_max=2.0)
+    pts = np.array([[0, 0, -2.0], [0, 0, -2.0001], [0, 0, -0.5], [0, 0, -0.4999], [0, 0, -1.0]], np.float32)
+    got = [c for c, _, _ in O.point_cell(p, ident(), pts)]
+    j = 4 * 8 + 4
+    assert got == [j, -1, j, -1, j]
