@@ -204,9 +204,12 @@ def test_fuse_then_move_equals_move_then_fuse():
 # --------------------------------------------------------------------------- harmonic fill
 
 def _hole(H, W, rng, frac=0.4, border=1):
+    """Random known cells; with border > 0 the outer `border` rings are known too (border = 0
+    leaves unknown cells on the crop border, where the fill is zero-flux)."""
     known = rng.random((H, W)) > frac
-    known[:border] = known[-border:] = True
-    known[:, :border] = known[:, -border:] = True
+    if border > 0:
+        known[:border] = known[-border:] = True
+        known[:, :border] = known[:, -border:] = True
     return known
 
 
@@ -227,6 +230,7 @@ def test_harmonic_fill_constant_and_maximum_principle():
     H, W = 20, 20
     known = _hole(H, W, rng, frac=0.6, border=0)
     known[0, 0] = True
+    assert not known[0].all() and not known.all()  # unknown cells on the border
     c = np.full((H, W), 1.25)
     out, _, _ = O.harmonic_fill(np.where(known, c, 0.0), known, tol=1e-13)
     np.testing.assert_allclose(out, 1.25, atol=1e-10)
@@ -274,3 +278,52 @@ def test_near_plane_is_strict(above, seen):
     assert out["vis"][j] == seen
     if seen:
         assert out["pix"][j] == 120 * 400 + 200
+
+
+def test_invalid_cells_never_occlude():
+    """Only valid cells can hide a cell (an unobserved cell has no height); a tall stale value in an
+    invalid cell on the walk changes nothing, the same value in a valid cell hides the target."""
+    W, res = 64, 0.25
+    m = flat_map(W, res, height=0.0)
+    sx, sy, hc = 10, 32, 2.0
+    R = synth.rot_y(math.radians(40)) @ synth.R_BODY_OPTICAL   # looking along +x, pitched down
+    pos = np.array([(sx - W // 2 + 0.5) * res, (sy - W // 2 + 0.5) * res, hc])
+    T = cam_pose(R, pos)
+    K = (300.0, 300.0, 1000.0, 1000.0)
+    j, q = sy * W + sx + 12, sy * W + sx + 6
+    assert m.fuse_image(2000, 2000, [], K, T)["vis"][j] == 1
+    m.h[q] = 100.0
+    assert m.fuse_image(2000, 2000, [], K, T)["vis"][j] == 0
+    m.valid[q] = 0
+    assert m.fuse_image(2000, 2000, [], K, T)["vis"][j] == 1
+
+
+def test_camera_outside_the_map_walks_from_the_clamped_edge_cell():
+    """The camera's cell is clamped into the map: a camera beyond the +x edge walks from the edge
+    cell, which is an end of every walk and so never occludes, even when it is a wall."""
+    W, res = 64, 0.25
+    m = flat_map(W, res, height=0.0)
+    sy, hc = 32, 2.0
+    hv = m.h.reshape(W, W)
+    hv[:, W - 1] = 1.0  # a wall along the edge column
+    R = synth.rot_z(math.pi) @ synth.rot_y(math.radians(40)) @ synth.R_BODY_OPTICAL  # looking along -x
+    pos = np.array([(W // 2) * res + 0.5, (sy - W // 2 + 0.5) * res, hc])
+    out = m.fuse_image(2000, 2000, [], (300.0, 300.0, 1000.0, 1000.0), cam_pose(R, pos))
+    for x in range(W - 12, W - 1):
+        assert out["vis"][sy * W + x] == 1, x
+
+
+def test_move_rounds_to_the_nearest_cell_and_keeps_counts():
+    rng = np.random.default_rng(6)
+    L = [O.Layer(3, O.LATEST)]
+    m, *_ = _filled(rng, layers=L)
+    W, res = 16, 0.25
+    a0, r0, h0 = m.n_acc.copy().reshape(W, W), m.n_rej.copy().reshape(W, W), m.h.copy().reshape(W, W)
+    m.move((0.7 * res, -0.6 * res))  # 0.7 and -0.6 cells round to (1, -1)
+    assert m.origin == (res, -res)
+    a, r, h = m.n_acc.reshape(W, W), m.n_rej.reshape(W, W), m.h.reshape(W, W)
+    # new (ix, iy) = old (ix + 1, iy - 1)
+    assert np.array_equal(a[1:, :W - 1], a0[:W - 1, 1:])
+    assert np.array_equal(r[1:, :W - 1], r0[:W - 1, 1:])
+    assert np.array_equal(h[1:, :W - 1], h0[:W - 1, 1:])
+    assert a0.sum() > 0

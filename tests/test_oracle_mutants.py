@@ -64,6 +64,20 @@ MUTANTS = {
           "if (!(rs >= c->range_min && rs < c->range_max * 0.5f)) return 0;")],
     "map edge off by one": [("if (!(qx >= -half && qx < half && qy >= -half && qy < half)) return 0;",
                              "if (!(qx >= -half && qx <= half && qy >= -half && qy < half)) return 0;")],
+    "visibility walk includes the target cell": [("for (int32_t m = 1; m + 1 < n; ++m) {", "for (int32_t m = 1; m < n; ++m) {")],
+    "ray parameter not normalised": [("float tq = (float)num / (float)den;", "float tq = (float)num;")],
+    "image rule counts two observations per pixel":
+        [("apply_rule(c, s, src[qs].layers[b], j, 1.0, S, S);", "apply_rule(c, s, src[qs].layers[b], j, 2.0, S, S);")],
+    "invalid cells occlude": [("        if (!s->valid[q]) continue;\n        int32_t num", "        int32_t num")],
+    "camera cell not clamped at the far edge": [("  if (!(qx <= half - 1.0f)) qx = half - 1.0f;", "")],
+    "move truncates instead of rounding":
+        [("long sx = lround((robot_xy[0] - s->origin[0]) / c->res);", "long sx = (long)((robot_xy[0] - s->origin[0]) / c->res);")],
+    "move drops the accepted counts": [("      s->n_acc[jn] = a[jo];", "      s->n_acc[jn] = 0;")],
+    "fill with a zero border instead of zero flux":
+        [("        if (x > 0) s += h[j - 1], ++m;\n        if (x + 1 < W) s += h[j + 1], ++m;\n"
+          "        if (y > 0) s += h[j - W], ++m;\n        if (y + 1 < H) s += h[j + W], ++m;\n        h[j] = s / m;",
+          "        if (x > 0) s += h[j - 1];\n        if (x + 1 < W) s += h[j + 1];\n"
+          "        if (y > 0) s += h[j - W];\n        if (y + 1 < H) s += h[j + W];\n        h[j] = s / 4;")],
 }
 
 
