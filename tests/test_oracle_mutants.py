@@ -129,6 +129,15 @@ UNET_MUTANTS = {
     "skip concatenation order swapped in the forward pass": ("np.concatenate([upsample(e4), e3], axis=3)",
                                                              "np.concatenate([e3, upsample(e4)], axis=3)"),
     "head bias dropped": ('out = d1 @ p["out.w"] + p["out.b"]', 'out = d1 @ p["out.w"]'),
+    "max pool takes the minimum": ("return v.max(axis=(2, 4))", "return v.min(axis=(2, 4))"),
+    "upsample shifted by a row": ("return x.repeat(2, axis=1).repeat(2, axis=2)",
+                                  "return np.roll(x.repeat(2, axis=1).repeat(2, axis=2), 1, axis=1)"),
+    "weight gradient halved": ("dw = (im2col(x).T @ d).reshape(w.shape)", "dw = (im2col(x).T @ d).reshape(w.shape) * 0.5"),
+    "bias gradient averaged": ("db = d.sum(axis=0)", "db = d.mean(axis=0)"),
+    "loss not normalised by the hidden count": ("return float((diff ** 2).sum() / cnt), 2.0 * diff / cnt",
+                                                "return float((diff ** 2).sum()), 2.0 * diff / cnt"),
+    "hidden mask ignored in the loss": ("diff = (fill + res - target) * hidden", "diff = (fill + res - target)"),
+    "decoder split at the skip width": ("du, de1 = split(dcat, c2)", "du, de1 = split(dcat, c1)"),
 }
 
 _RUN_UNET = r'''

@@ -90,3 +90,17 @@ def test_zero_output_layer_returns_fill():
     assert np.all(res == 0)
     pred = fill + res
     assert np.array_equal(pred, fill)
+
+
+def test_loss_counts_hidden_cells_only():
+    """Masked MSE: the mean of (fill + residual - target)^2 over hidden cells; visible cells add
+    nothing and get no gradient."""
+    rng = np.random.default_rng(9)
+    res, fill, target = rng.normal(size=(3, 2, 6, 5))
+    hidden = np.zeros((2, 6, 5))
+    hidden[0, 1, 2] = hidden[1, 4, 0] = hidden[1, 5, 4] = 1.0
+    loss, g = U.loss_and_grad_out(res, fill, target, hidden)
+    d = (fill + res - target)[hidden == 1]
+    assert loss == pytest.approx((d ** 2).sum() / 3, rel=1e-12)
+    assert np.all(g[hidden == 0] == 0)
+    np.testing.assert_allclose(g[hidden == 1], 2 * d / 3, rtol=1e-12)
