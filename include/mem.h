@@ -10,8 +10,8 @@
  *     cnt" and "height update");
  *   - Sec. III-C (Fusion algorithms): Latest (Eq. 1), Exponential averaging
  *     (Eq. 2), Gaussian Bayesian inference (Eqs. 3-7), Dirichlet Bayesian
- *     inference (Eqs. 8-12), and a class-max layer (Sec. V-B's
- *     "highest class probability" colouring).
+ *     inference (Eqs. 8-12), and a class-max layer (the most probable
+ *     class of a cell, which Sec. V-B uses to colour the semantic map).
  *
  * Memory and streams
  *   - The library owns every map's device memory (allocated in
@@ -80,7 +80,7 @@ typedef enum {
 
 typedef enum { MEM_F32 = 0, MEM_BF16 = 1, MEM_F16 = 2, MEM_U8 = 3 } mem_dtype;
 
-/* A multi-modal layer ("task-agnostic information container", Sec. III-A).
+/* A multi-modal layer (Sec. III-A: a layer that holds data of any modality).
  * channels = K classes or d feature dimensions of the observations.
  * dtype    = storage of the layer values (MEM_F32, MEM_BF16 or MEM_F16);
  *            accumulation is float32 whatever the storage. CLASSMAX and
@@ -138,18 +138,31 @@ typedef struct {
 #define MEM_PART_OBSERVED 3 /* uint8, 1 once the layer of the cell was fused   */
 
 /* Create `cfg->n_maps` maps centred on the world origin, every cell empty.
- * Returns MEM_ERR_ARG for an invalid config, MEM_ERR_OOM if device memory
- * runs out. */
+ * The map is the 2.5D grid of Sec. III-A: pure geometric layers (elevation,
+ * its variance, validity, the accepted / rejected point counts of the
+ * predecessor's height update) plus the configured multi-modal layers, which hold
+ * information of any modality, each bound to one fusion rule of Sec. III-C. Layout in HBM: planar arrays of n_maps * W * W cells.
+ * Allocates synchronously on the current device (no stream); the library owns
+ * the memory until mem_destroy_map. Returns MEM_ERR_ARG for an invalid config
+ * (nothing allocated), MEM_ERR_OOM if device memory runs out. */
 mem_status mem_create_map(const mem_map_config *cfg, mem_map **out);
 mem_status mem_destroy_map(mem_map *m);
 
-/* Robot-centric re-centring (the map follows the robot): shift map
- * `map_index` by whole cells so its centre is the cell centre nearest to
- * robot_xy (host, world metres); cells that enter are reset. O(entering
- * cells) on the device. */
+/* Robot-centric re-centring (Sec. I and III-A: the map is centred on the
+ * robot and moves with it): shift map `map_index` by whole cells so its centre
+ * is the cell centre nearest to robot_xy (host, float64 world metres); the
+ * shift is round((robot - origin) / res) per axis; cells that enter are reset
+ * to every layer's initial state. O(entering cells) on the device (ring-buffer
+ * offsets). Errors: MEM_ERR_ARG (bad index, non-finite or huge move; state
+ * unchanged), MEM_ERR_CUDA. */
 mem_status mem_move_map(mem_map *m, int32_t map_index, const double robot_xy[2], void *stream);
 
-/* Fuse one point cloud into a single-map object (n_maps == 1).
+/* Fuse one point cloud into a single-map object (n_maps == 1): Sec. III-B
+ * (a point is associated to the cell under its horizontal coordinates, and
+ * updates the elevation following the predecessor paper -- Table I rows
+ * "point trsf. & z err. cnt" and "height update") and Sec. III-C (each
+ * source's channels are fused into its layers by the layer's rule, Eqs. 1-12;
+ * the N_j points of a cell in one call are one observation set).
  *   n        number of points (0 allowed), n < 2^30
  *   xyz      device float32 [n][3], sensor frame; non-finite rows are dropped
  *   sources  host array of n_sources (<= MEM_MAX_SOURCES) descriptors whose
@@ -175,9 +188,12 @@ mem_status mem_fuse_pointcloud_host(mem_map *m, int64_t n, const float *xyz, int
                                     void *stream);
 
 /* Fuse n_maps independent clouds into the n_maps maps of one object in one
- * pass. offsets: host int64 [n_maps + 1] CSR offsets into xyz and the
- * source rows; T_map_sensor: host float64 [n_maps][16]. Results equal
- * n_maps separate single-map fuses. */
+ * pass: the same per-map update as mem_fuse_pointcloud (Sec. III-B, III-C),
+ * for many maps at once (independent robots or simulated environments; the
+ * paper fuses one map). offsets: host int64 [n_maps + 1] CSR offsets into xyz
+ * and the source rows (device, as for mem_fuse_pointcloud); T_map_sensor:
+ * host float64 [n_maps][16]. Results equal n_maps separate single-map fuses.
+ * Errors as mem_fuse_pointcloud; offsets must start at 0 and not decrease. */
 mem_status mem_fuse_pointcloud_batch(mem_map *m, const int64_t *offsets, const float *xyz,
                                      int32_t n_sources, const mem_source *sources,
                                      const double *T_map_sensor, void *stream);
@@ -195,7 +211,12 @@ mem_status mem_fuse_image(mem_map *m, int32_t map_index, int32_t H, int32_t Wi, 
                           uint8_t *vis_out, int32_t *pix_out, void *stream);
 
 /* Copy one layer (part) of map `map_index` into device memory `dst`, in
- * logical cell order (cell j = iy * W + ix, values per cell contiguous). */
+ * logical cell order (cell j = iy * W + ix, values per cell contiguous): the
+ * map's layers as the plugins of Sec. III-D and external consumers read them.
+ * MEM_PART_THETA of a DIRICHLET layer is the posterior mean alpha / sum(alpha)
+ * (Eq. 11). An unobserved cell reads as its layer's initial state. dst is
+ * caller-owned, sized W*W*values*element size; asynchronous on `stream`.
+ * Errors: MEM_ERR_ARG for a bad index, layer or part (nothing queued). */
 mem_status mem_get_layer(mem_map *m, int32_t map_index, int32_t layer, int32_t part, void *dst,
                          void *stream);
 /* Inverse of mem_get_layer (MEM_PART_THETA not settable): checkpoint restore
@@ -266,8 +287,8 @@ mem_status mem_inpaint_diffusion(int32_t n_crops, int32_t H, int32_t W, const fl
                                  const uint8_t *known, float *h_out, float tol, int32_t max_iters,
                                  int32_t *iters_out, void *stream);
 
-/* Learned inpainting (the paper's post-processing plugins "take map layers as
- * input and generate a new layer", Sec. III-D; the network layout is this
+/* Learned inpainting (Sec. III-D: post-processing plugins may run neural
+ * networks on map layers to produce a new layer; the network layout is this
  * library's): a U-Net over crops of map layers predicting a residual that is
  * added to the diffusion fill. Four levels of widths[0..3] channels, two 3x3
  * convolutions + ReLU per level, 2x2 max-pooling, nearest upsampling with
@@ -309,11 +330,13 @@ mem_status mem_unet_check(mem_unet *u, void *stream);
  * another framework's memory pool, real-time loops that forbid allocation
  * after start-up, hosts whose device allocator is owned by someone else.
  * It fuses one point cloud into caller-owned height layers (the height update
- * with outlier gate of mem_fuse_pointcloud, no multi-modal layers) and
- * allocates nothing: no cudaMalloc, cudaFree, pinned memory or allocating
- * library routine. Its sort and segment scratch is one file-scope device
- * array sized for MEM_NOALLOC_MAX_POINTS points (about 22 MB, held by every
- * GPU that loads the library until the process exits).
+ * with outlier gate and the time-dependent variance growth of
+ * mem_fuse_pointcloud, no multi-modal layers) and allocates nothing: no
+ * cudaMalloc, cudaFree, pinned memory or allocating library routine. Its sort
+ * and segment scratch is one file-scope device array sized for
+ * MEM_NOALLOC_MAX_POINTS points (about 22 MB, held by every GPU that loads
+ * the library until the process exits); the call's parameters reach the
+ * device as kernel arguments.
  *   cfg       host; n_maps must be 1 and n_layers 0; max_points is ignored
  *   origin_xy host; world xy of the map centre (cell W/2 lower corner)
  *   n         points, 0 <= n <= MEM_NOALLOC_MAX_POINTS (larger: MEM_ERR_ARG)
@@ -326,12 +349,19 @@ mem_status mem_unet_check(mem_unet *u, void *stream);
  * sets kernel attributes; make that first call before any stream capture.
  * Every call shares the one array and overwrites it: calls that overlap on
  * the GPU (other streams, other threads) race and must be serialised by the
- * caller. */
+ * caller. A call whose bounded device wait runs out leaves the layers as they
+ * were and returns MEM_OK (the failure happens after the call returned); the
+ * next call starts afresh, and mem_noalloc_check reports the failure. */
 #define MEM_NOALLOC_MAX_POINTS (1 << 18)
 mem_status mem_fuse_pointcloud_noalloc(const mem_map_config *cfg, const double origin_xy[2],
                                        int64_t n, const float *xyz, const double T_map_sensor[16],
                                        float *h, float *var, uint32_t *valid, uint32_t *n_acc,
                                        uint32_t *n_rej, void *stream);
+/* Companion of mem_fuse_pointcloud_noalloc (no paper counterpart, allocates
+ * nothing): synchronises `stream`, then returns MEM_ERR_TIMEOUT (and clears
+ * the record) if an allocation-free fuse on the current device timed out in a
+ * bounded device wait since the previous check, MEM_OK otherwise. */
+mem_status mem_noalloc_check(void *stream);
 /* Thread-local description of the last error. */
 const char *mem_last_error(void);
 

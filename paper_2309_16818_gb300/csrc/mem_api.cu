@@ -710,7 +710,10 @@ static mem_status run_points(Map* m, int nm, const int64_t* offsets, int64_t n, 
     CK(cudaEventRecord(ready, job_st), "job upload record");
     CK(cudaStreamWaitEvent(st, ready, 0), "job upload wait");
   }
-  if (n == 0) return MEM_OK;
+  if (n == 0) {  // no points: only the time-dependent variance growth of the valid cells
+    CK(launch_time_update(m, st), "time update launch");
+    return MEM_OK;
+  }
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   if (graph && st) cudaStreamIsCapturing(st, &cap);
   if (graph && st && cap == cudaStreamCaptureStatusNone && m->use_graph && !m->prof_on) {

@@ -88,6 +88,8 @@ cudaError_t alloc_scratch(Map* m, int64_t cap);
 void free_scratch(Map* m);
 int key_bits_for(const Map* m);
 cudaError_t prepare_kernels();
+// time-dependent variance growth of every valid cell (no-op when time_var == 0)
+cudaError_t launch_time_update(Map* m, cudaStream_t st);
 // stage layout and rule-layer lists of a point-path call (job.src, n_src and
 // the raw slot length `acc_raw` set), as the fuse kernel reads them
 void build_fuse_tables(memk::PointJob& job, int acc_raw, const mem_map_config& cfg);

@@ -1249,8 +1249,17 @@ __global__ void k_time_update(MapDev md, int64_t cells) {
 namespace memh {
 using namespace memk;
 
+// Kernel attributes are per device: the current device's index selects the
+// entry of these tables (set by prepare_kernels with that device current).
+constexpr int kMaxDevices = 128;
 // resident CTAs per SM of the tile fuse kernel (its persistent grid)
-static int g_sums_ctas_per_sm = 1;
+static int g_sums_ctas_per_sm[kMaxDevices] = {};
+
+static int current_device() {
+  int d = 0;
+  if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= kMaxDevices) d = 0;
+  return d;
+}
 
 template <int RB>
 static size_t sort_smem() {
@@ -1260,12 +1269,22 @@ static size_t sort_smem() {
 
 template <int RB>
 static cudaError_t set_attrs() {
-  static bool done = false;
-  if (done) return cudaSuccess;
+  static bool done[kMaxDevices] = {};
+  const int dev = current_device();
+  if (done[dev]) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(k_onesweep<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)sort_smem<RB>());
-  if (e == cudaSuccess) done = true;
+  if (e == cudaSuccess) done[dev] = true;
   return e;
+}
+
+cudaError_t launch_time_update(Map* m, cudaStream_t st) {
+  const MapDev& md = m->md;
+  if (md.time_var == 0.f) return cudaSuccess;
+  ProfScope ps(m, kProfTime, st);
+  const int64_t cells = (int64_t)md.n_maps * md.W2;
+  k_time_update<<<m->n_sm * m->tune.blocks_per_sm, 256, 0, st>>>(md, cells);
+  return cudaGetLastError();
 }
 
 template <int RB>
@@ -1289,26 +1308,25 @@ static cudaError_t launch_rb(Map* m, const PointJob* d_job, cudaStream_t st) {
   }
   {
     ProfScope ps(m, kProfFuseTiles, st);
-    k_fuse_tiles<<<sms * g_sums_ctas_per_sm, kFT, sizeof(SumSmem), st>>>(md, d_job, P & 1);
+    const int cps = g_sums_ctas_per_sm[current_device()];
+    k_fuse_tiles<<<sms * (cps > 0 ? cps : 1), kFT, sizeof(SumSmem), st>>>(md, d_job, P & 1);
   }
   {
     ProfScope ps(m, kProfFuseCross, st);
     k_fuse_cross<<<sms * 8, 128, 0, st>>>(md, d_job);
   }
-  if (md.time_var != 0.f) {
-    ProfScope ps(m, kProfTime, st);
-    const int64_t cells = (int64_t)md.n_maps * md.W2;
-    k_time_update<<<sms * bps, 256, 0, st>>>(md, cells);
-  }
-  return cudaGetLastError();
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_time_update(m, st);
 }
 
 cudaError_t prepare_kernels() {
+  const int dev = current_device();
   cudaError_t e = cudaFuncSetAttribute(k_fuse_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)sizeof(SumSmem));
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_sums_ctas_per_sm, k_fuse_tiles, kFT, sizeof(SumSmem));
-  if (g_sums_ctas_per_sm < 1) g_sums_ctas_per_sm = 1;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_sums_ctas_per_sm[dev], k_fuse_tiles, kFT, sizeof(SumSmem));
+  if (g_sums_ctas_per_sm[dev] < 1) g_sums_ctas_per_sm[dev] = 1;
   if (e == cudaSuccess) e = set_attrs<8>();
   if (e == cudaSuccess) e = set_attrs<9>();
   if (e == cudaSuccess) e = set_attrs<10>();

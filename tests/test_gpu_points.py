@@ -156,6 +156,51 @@ def test_time_and_outlier_variance(torch):
         compare_states(gpu_state(g), o, what=f"variance growth pose {k}")
 
 
+def test_time_variance_on_empty_clouds_and_untouched_cells(torch):
+    """time_var ages every valid cell once per call, touched or not: a full scan, an empty
+    cloud (device and host-buffer entry points), a few points that leave almost every valid
+    cell untouched, and an empty batched call over three maps; each call starts both sides
+    from the oracle's state and compares every cell."""
+    c = synth.config2(n_poses=2, scale=0.2)
+    g, o = make_pair(c["W"], c["res"], multimodal_layers(), outlier_var=0.01, time_var=1e-4)
+    s0, s1 = c["scans"]
+    few = slice(0, 40)
+    empty_np = np.zeros((0, 3), np.float32)
+    steps = [("scan", s0.xyz, s0.T, cloud_sources_np(s0), False),
+             ("empty", empty_np, s0.T, [], False),
+             ("empty host", empty_np, s0.T, [], True),
+             ("few points", s1.xyz[few], s1.T, [(s1.rgb[few], [0]), (s1.probs[few], [1, 2, 3])], False)]
+    for what, xyz, T, src, host in steps:
+        upload_state(g, o)
+        o.fuse_points(xyz, T, src)
+        if host:
+            g.fuse_pointcloud_host(torch.from_numpy(np.ascontiguousarray(xyz)).pin_memory(), T,
+                                   [(torch.from_numpy(np.ascontiguousarray(a)).pin_memory(), L) for a, L in src])
+        else:
+            g.fuse_pointcloud(torch.from_numpy(np.ascontiguousarray(xyz)).cuda(), T,
+                              [(torch.from_numpy(np.ascontiguousarray(a)).cuda(), L) for a, L in src])
+        g.check()
+        compare_states(gpu_state(g), o, what=what)
+    assert o.valid.sum() > 1000
+    # batched: three maps, one cloud for map 0 then an all-empty call
+    B = 3
+    gb, _ = make_pair(c["W"], c["res"], [], n_maps=B, time_var=1e-4)
+    ob = [O.OracleMap(O.Params(W=c["W"], res=c["res"], time_var=1e-4)) for _ in range(B)]
+    for rnd in range(2):
+        n0 = s0.n if rnd == 0 else 0
+        offsets = np.array([0, n0, n0, n0], np.int64)
+        xyz = s0.xyz[:n0]
+        ob[0].fuse_points(xyz, s0.T)
+        for b in (1, 2):
+            ob[b].fuse_points(empty_np, s0.T)
+        gb.fuse_pointcloud_batch(offsets, torch.from_numpy(np.ascontiguousarray(xyz)).cuda(),
+                                 np.stack([s0.T] * B))
+        gb.check()
+        for b in range(B):
+            compare_states(gpu_state(gb, b), ob[b], what=f"batched round {rnd} map {b}")
+    assert ob[0].valid.sum() > 1000
+
+
 def test_bf16_and_f16_feature_storage(torch):
     """Gaussian feature layers stored in BF16 / F16 / F32, fed BF16 point features."""
     c = synth.config4(n_maps=1, n_lo=40_000, n_hi=40_001)
