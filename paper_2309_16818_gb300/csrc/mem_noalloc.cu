@@ -3,9 +3,9 @@
 // lives in one file-scope __device__ array of fixed size instead.
 //
 // Callers that cannot allocate -- code running inside another framework's
-// memory pool or a CUDA-graph-captured region, real-time loops that forbid
-// allocation after start-up, or hosts whose allocator is owned by someone
-// else -- can still run the map update on buffers they already hold.
+// memory pool, real-time loops that forbid allocation after start-up, or
+// hosts whose device allocator is owned by someone else -- can still run the
+// map update on buffers they already hold.
 #include <math.h>
 #include <stddef.h>
 #include <string.h>
@@ -30,6 +30,9 @@ constexpr int64_t kVals1 = kVals0 + up(kMaxPts + 4);
 constexpr int64_t kHist = kVals1 + up(kMaxPts + 4);           // 4*1024 digits + 16 counters
 constexpr int64_t kLook = kHist + up(4 * 1024 + 16);           // 4 passes x tiles x 1024
 constexpr int64_t kPart = kLook + up(4 * kTiles * 1024);       // fuse tile tables + slots
+// error words: [0] a bounded wait of this call ran out (the point kernels then
+// return at entry), [1] fault injection (always 0 here), [2] sticky record of
+// timeouts since the last mem_noalloc_check
 constexpr int64_t kErr = kPart + up(memk::fuse_scratch_words(kMaxPts, memk::kSlotHdr));
 constexpr int64_t kJob = kErr + up(1);
 struct JobBlock {
@@ -45,6 +48,45 @@ static __device__ __align__(256) u32 g_noalloc_scratch[kWords];
 std::mutex g_mu;
 void* g_addr[128] = {};
 int g_nsm[128] = {};
+
+// Writes the call's job block into the static array from the kernel's own
+// parameters (passed by value, so nothing is read from host memory after the
+// launch), and starts the call with a clear error word: a timeout of an
+// earlier call is kept in the sticky word [2] instead.
+__global__ void k_noalloc_job(JobBlock jb, u32* dst, int* err) {
+  const u32* src = reinterpret_cast<const u32*>(&jb);
+  constexpr int kw = (int)(sizeof(JobBlock) / 4);
+  for (int i = threadIdx.x; i < kw; i += blockDim.x) dst[i] = src[i];
+  if (threadIdx.x == 0) {
+    if (err[0]) err[2] = err[0];
+    err[0] = 0;
+    err[1] = 0;
+  }
+}
+static_assert(sizeof(JobBlock) % 4 == 0 && sizeof(JobBlock) <= 4000, "job block fits the kernel parameters");
+
+// the array's device address on the current device (looked up once per device)
+mem_status noalloc_base(int* dev_out, void** base, int* n_sm) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return memh::api_cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= 128) return memh::api_fail(MEM_ERR_STATE, "device index out of range");
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (!g_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return memh::api_cuda_fail(e, "cudaGetSymbolAddress");
+    e = memh::prepare_kernels();
+    if (e != cudaSuccess) return memh::api_cuda_fail(e, "kernel attributes");
+    e = cudaDeviceGetAttribute(&g_nsm[dev], cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return memh::api_cuda_fail(e, "device attribute");
+    g_addr[dev] = p;
+  }
+  *dev_out = dev;
+  *base = g_addr[dev];
+  if (n_sm) *n_sm = g_nsm[dev];
+  return MEM_OK;
+}
 
 }  // namespace
 
@@ -69,27 +111,10 @@ extern "C" mem_status mem_fuse_pointcloud_noalloc(const mem_map_config* cfg, con
     if (!isfinite(T_map_sensor[k])) return memh::api_fail(MEM_ERR_ARG, "pose not finite");
 
   // set-up, once per device, with that device current
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return memh::api_cuda_fail(e, "cudaGetDevice");
-  if (dev < 0 || dev >= 128) return memh::api_fail(MEM_ERR_STATE, "device index out of range");
+  int dev = 0, n_sm = 0;
   void* base = nullptr;
-  int n_sm = 0;
-  {
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[dev]) {
-      void* p = nullptr;
-      e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-      if (e != cudaSuccess) return memh::api_cuda_fail(e, "cudaGetSymbolAddress");
-      e = memh::prepare_kernels();
-      if (e != cudaSuccess) return memh::api_cuda_fail(e, "kernel attributes");
-      e = cudaDeviceGetAttribute(&g_nsm[dev], cudaDevAttrMultiProcessorCount, dev);
-      if (e != cudaSuccess) return memh::api_cuda_fail(e, "device attribute");
-      g_addr[dev] = p;
-    }
-    base = g_addr[dev];
-    n_sm = g_nsm[dev];
-  }
+  mem_status ms = noalloc_base(&dev, &base, &n_sm);
+  if (ms != MEM_OK) return ms;
   u32* w = (u32*)base;
 
   memh::Map m;  // host-side description only; owns nothing
@@ -149,10 +174,31 @@ extern "C" mem_status mem_fuse_pointcloud_noalloc(const mem_map_config* cfg, con
   hj.mc.t[1] = (float)(T_map_sensor[7] - origin_xy[1]);
   hj.mc.t[2] = (float)T_map_sensor[11];
   cudaStream_t st = (cudaStream_t)stream;
-  e = cudaMemcpyAsync(d_job, &hj, sizeof(hj), cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return memh::api_cuda_fail(e, "job upload");
-  if (n == 0) return MEM_OK;
-  e = memh::launch_point_fuse(&m, (const PointJob*)d_job, st);
+  k_noalloc_job<<<1, 128, 0, st>>>(hj, d_job, md.err);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return memh::api_cuda_fail(e, "allocation-free job launch");
+  // no points: only the time-dependent variance growth of the valid cells
+  e = n == 0 ? memh::launch_time_update(&m, st) : memh::launch_point_fuse(&m, (const PointJob*)d_job, st);
   if (e != cudaSuccess) return memh::api_cuda_fail(e, "allocation-free fuse launch");
+  return MEM_OK;
+}
+
+extern "C" mem_status mem_noalloc_check(void* stream) {
+  int dev = 0;
+  void* base = nullptr;
+  mem_status ms = noalloc_base(&dev, &base, nullptr);
+  if (ms != MEM_OK) return ms;
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return memh::api_cuda_fail(e, "stream synchronize");
+  int* err = (int*)((u32*)base + kErr);
+  int w[3] = {0, 0, 0};
+  e = cudaMemcpy(w, err, sizeof(w), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return memh::api_cuda_fail(e, "read error words");
+  if (w[0] || w[2]) {
+    e = cudaMemset(err, 0, sizeof(w));
+    if (e != cudaSuccess) return memh::api_cuda_fail(e, "clear error words");
+    return memh::api_fail(MEM_ERR_TIMEOUT, "an allocation-free fuse timed out in a bounded device wait "
+                                           "and left the layers of that call unchanged");
+  }
   return MEM_OK;
 }

@@ -30,7 +30,8 @@ EXPORTS = ["mem_create_map", "mem_destroy_map", "mem_move_map", "mem_fuse_pointc
            "mem_set_profiling", "mem_get_profile", "mem_get_stats", "mem_fuse_pointcloud_noalloc",
            "mem_autotune_batch", "mem_inpaint_diffusion", "mem_unet_create", "mem_unet_destroy",
            "mem_unet_param_count", "mem_unet_set_params", "mem_unet_get_params", "mem_unet_forward",
-           "mem_unet_gradients", "mem_unet_train_step", "mem_unet_check", "mem_inject_fault"]
+           "mem_unet_gradients", "mem_unet_train_step", "mem_unet_check", "mem_inject_fault",
+           "mem_noalloc_check"]
 NOALLOC_MAX_POINTS = 1 << 18
 PROFILE_SLOTS = ["key", "digit_scan", "radix_sort", "unused3", "fuse_tiles", "fuse_cross",
                  "time_var", "image", "move"]
@@ -92,6 +93,7 @@ def lib():
             "mem_unet_gradients": [P, I32, I32, I32, P, P, P, P, I64, P, P, P],
             "mem_unet_train_step": [P, I32, I32, I32, P, P, P, P, I64, C.c_float, P, P],
             "mem_unet_check": [P, P], "mem_inject_fault": [P, I32],
+            "mem_noalloc_check": [P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -150,6 +152,12 @@ def fuse_pointcloud_noalloc(W, res, xyz, T, h, var, valid, n_acc, n_rej, origin=
                                           C.c_void_p(h.data_ptr()), C.c_void_p(var.data_ptr()),
                                           C.c_void_p(valid.data_ptr()), C.c_void_p(n_acc.data_ptr()),
                                           C.c_void_p(n_rej.data_ptr()), _stream(stream)))
+
+
+def noalloc_check(stream=None):
+    """Synchronise and raise MemError (ERR_TIMEOUT) if an allocation-free fuse on the current
+    device timed out in a bounded device wait since the previous check (mem_noalloc_check)."""
+    _ck(lib().mem_noalloc_check(_stream(stream)))
 
 
 def inpaint_diffusion(h, known, tol=1e-6, max_iters=20000, out=None, stream=None):
