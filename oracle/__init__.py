@@ -61,7 +61,9 @@ class Cfg(C.Structure):
                 ("range_max", C.c_float), ("z_near", C.c_float), ("round_store", C.c_int32),
                 ("channels", C.c_int32 * MAX_LAYERS), ("rule", C.c_int32 * MAX_LAYERS),
                 ("store", C.c_int32 * MAX_LAYERS), ("w", C.c_double * MAX_LAYERS),
-                ("var_meas", C.c_double * MAX_LAYERS), ("alpha0", C.c_double * MAX_LAYERS)]
+                ("var_meas", C.c_double * MAX_LAYERS), ("alpha0", C.c_double * MAX_LAYERS),
+                ("drift_alpha", C.c_double), ("drift_min_points", C.c_int32),
+                ("ray_cleanup", C.c_int32), ("ray_margin", C.c_float)]
 
 
 class State(C.Structure):
@@ -97,6 +99,7 @@ def lib():
         L.orc_fuse_image.restype = C.c_int64
         L.orc_harmonic_fill.argtypes = [C.c_int32, C.c_int32, P, P, C.c_double, C.c_int32, P]
         L.orc_harmonic_fill.restype = C.c_int32
+        L.orc_last_fuse_info.argtypes = [P, P, P]
         _lib = L
     return _lib
 
@@ -134,6 +137,10 @@ class Params:
     range_min: float = 0.1
     range_max: float = 50.0
     z_near: float = 0.05
+    drift_alpha: float = 0.0
+    drift_min_points: int = 1
+    ray_cleanup: bool = False
+    ray_margin: float = 0.1
 
 
 def _dtype_code(a: np.ndarray, bf16: bool = False) -> int:
@@ -160,8 +167,9 @@ class OracleMap:
         c.n_layers = len(p.layers)
         c.res = p.res
         for k in ("sigma0", "sigma1", "gate_lambda", "outlier_var", "time_var", "range_min",
-                  "range_max", "z_near"):
+                  "range_max", "z_near", "drift_alpha", "drift_min_points", "ray_margin"):
             setattr(c, k, getattr(p, k))
+        c.ray_cleanup = int(bool(p.ray_cleanup))
         c.round_store = int(round_store)
         for i, L in enumerate(p.layers):
             c.channels[i] = L.channels
@@ -237,7 +245,10 @@ class OracleMap:
                                      C.cast(src, C.c_void_p), _p(T),
                                      _p(near) if near is not None else None,
                                      _p(cells) if cells is not None else None)
-        return dict(kept=kept, cells=cells, near=near)
+        drift, dn, cleared = C.c_double(), C.c_int64(), C.c_int64()
+        lib().orc_last_fuse_info(C.byref(drift), C.byref(dn), C.byref(cleared))
+        return dict(kept=kept, cells=cells, near=near, drift=drift.value, drift_points=dn.value,
+                    cleared=cleared.value)
 
     def fuse_image(self, H: int, Wi: int, sources, K, T):
         keep = []
@@ -259,7 +270,8 @@ class OracleMap:
 def point_cell(p: Params, T: np.ndarray, pts: np.ndarray, origin=(0.0, 0.0)):
     """Cell index (or -1), map-frame z and measurement variance of each point."""
     m = OracleMap(Params(p.W, p.res, [], p.sigma0, p.sigma1, p.gate_lambda, p.outlier_var,
-                         p.time_var, p.range_min, p.range_max, p.z_near))
+                         p.time_var, p.range_min, p.range_max, p.z_near, p.drift_alpha,
+                         p.drift_min_points, p.ray_cleanup, p.ray_margin))
     Rt = np.empty(12, np.float32)
     o = np.array(origin, dtype=np.float64)
     T = np.ascontiguousarray(T, dtype=np.float64)

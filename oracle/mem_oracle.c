@@ -193,6 +193,29 @@ static void apply_rule(const orc_cfg *c, orc_state *s, int l, int64_t j, double 
 /* ------------------------------------------------------------------------ */
 /* point-cloud update                                                       */
 
+static _Thread_local double g_last_drift;
+static _Thread_local int64_t g_last_drift_points, g_last_cleared;
+
+void orc_last_fuse_info(double *drift, int64_t *drift_points, int64_t *cleared) {
+  if (drift) *drift = g_last_drift;
+  if (drift_points) *drift_points = g_last_drift_points;
+  if (cleared) *cleared = g_last_cleared;
+}
+
+/* The map cell of a position relative to the map centre, clamped into the map
+ * (the sensor or camera cell of a visibility walk). */
+static void clamped_cell(const orc_cfg *c, float px, float py, int32_t *cx, int32_t *cy) {
+  float res = (float)c->res;
+  float half = (float)(c->W / 2);
+  float qx = floorf(px / res), qy = floorf(py / res);
+  if (!(qx >= -half)) qx = -half;
+  if (!(qx <= half - 1.0f)) qx = half - 1.0f;
+  if (!(qy >= -half)) qy = -half;
+  if (!(qy <= half - 1.0f)) qy = half - 1.0f;
+  *cx = (int32_t)qx + c->W / 2;
+  *cy = (int32_t)qy + c->W / 2;
+}
+
 int64_t orc_fuse_points(const orc_cfg *c, orc_state *s, int64_t n, const float *xyz, int32_t n_src,
                         const orc_src *src, const double T[16], uint8_t *near_gate,
                         int32_t *cell_out) {
@@ -213,6 +236,51 @@ int64_t orc_fuse_points(const orc_cfg *c, orc_state *s, int64_t n, const float *
   }
   float lam2 = c->gate_lambda * c->gate_lambda;
   int64_t kept = 0;
+
+  /* z error count and drift compensation (Table I rows "point trsf. & z err. cnt" and "drift
+     compensation"; the paper defers both to its predecessor, this is the reading stated in the
+     design notes): e = z - h for every kept point whose cell is valid before this call and
+     that the outlier gate accepts; if at least drift_min_points such points exist, every
+     valid height moves by drift_alpha * mean(e), so the map follows the new cloud before the
+     height update gates against it */
+  double drift = 0.0;
+  int64_t drift_n = 0;
+  if (c->drift_alpha != 0.0) {
+    double esum = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+      int32_t j;
+      float z, vm;
+      if (!orc_point_cell(c, Rt, &xyz[3 * i], &j, &z, &vm)) continue;
+      if (!s->valid[j]) continue;
+      float d = z - (float)s->h[j];
+      if (d * d > lam2 * ((float)s->var[j] + vm)) continue;
+      esum += (double)d;
+      ++drift_n;
+    }
+    if (drift_n > 0 && drift_n >= c->drift_min_points) {
+      drift = (double)(float)(c->drift_alpha * (esum / (double)drift_n));
+      for (int64_t j = 0; j < W2; ++j)
+        if (s->valid[j]) s->h[j] = store_round(c, ORC_F32, s->h[j] + drift);
+    }
+  }
+  g_last_drift = drift;
+  g_last_drift_points = drift_n;
+  g_last_cleared = 0;
+
+  /* what the ray-cast clean-up needs: the state the gate sees, and every accepted point */
+  double *h_gate = NULL;
+  uint8_t *valid_gate = NULL;
+  int32_t *acc_cell = NULL;
+  float *acc_z = NULL;
+  int64_t n_accpt = 0;
+  if (c->ray_cleanup) {
+    h_gate = malloc((size_t)W2 * sizeof(double));
+    valid_gate = malloc((size_t)W2);
+    memcpy(h_gate, s->h, (size_t)W2 * sizeof(double));
+    memcpy(valid_gate, s->valid, (size_t)W2);
+    acc_cell = malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+    acc_z = malloc((size_t)(n > 0 ? n : 1) * sizeof(float));
+  }
 
   /* association and accumulation, in input order */
   for (int64_t i = 0; i < n; ++i) {
@@ -244,6 +312,11 @@ int64_t orc_fuse_points(const orc_cfg *c, orc_state *s, int64_t n, const float *
       ++na[j];
       Sw[j] += 1.0 / (double)vm;
       Swz[j] += (double)z / (double)vm;
+      if (c->ray_cleanup) {
+        acc_cell[n_accpt] = j;
+        acc_z[n_accpt] = z;
+        ++n_accpt;
+      }
     }
     for (int q = 0; q < n_src; ++q) {
       int C = src[q].channels;
@@ -281,6 +354,47 @@ int64_t orc_fuse_points(const orc_cfg *c, orc_state *s, int64_t n, const float *
         apply_rule(c, s, src[q].layers[b], j, (double)np[j], &acc[q].sum[j * C], &acc[q].mx[j * C]);
     }
   }
+  /* ray-cast clean-up (the "ray cast" of Table I's "height update & ray cast"; reading stated
+     in the design notes): every accepted point casts the ray from the sensor to itself over the
+     integer Bresenham line of cells from the sensor's cell (clamped into the map) to its own
+     cell, both ends excluded. An intermediate cell q that was valid for the gate is passed
+     below when its height exceeds the ray height there by more than ray_margin:
+       ray = z_s + t_q (z - z_s),  t_q = ((q - s).(e - s)) / |e - s|^2.
+     A passed-below cell that accepted no point of this call is stale and becomes invalid. */
+  if (c->ray_cleanup) {
+    int32_t sx, sy;
+    clamped_cell(c, Rt[9], Rt[10], &sx, &sy);
+    float zs = Rt[11];
+    uint8_t *mark = calloc((size_t)W2, 1);
+    int32_t *line = malloc((size_t)(4 * c->W + 8) * sizeof(int32_t));
+    for (int64_t a = 0; a < n_accpt; ++a) {
+      int32_t ex = acc_cell[a] % c->W, ey = acc_cell[a] / c->W;
+      int32_t dxs = ex - sx, dys = ey - sy;
+      int32_t den = dxs * dxs + dys * dys;
+      int32_t nl = orc_bresenham(sx, sy, ex, ey, line, 2 * c->W + 4);
+      for (int32_t m = 1; m + 1 < nl; ++m) {
+        int32_t qx = line[2 * m], qy = line[2 * m + 1];
+        int64_t q = (int64_t)qy * c->W + qx;
+        if (!valid_gate[q]) continue;
+        int32_t num = (qx - sx) * dxs + (qy - sy) * dys;
+        float tq = (float)num / (float)den;
+        float ray = fmaf(tq, acc_z[a] - zs, zs);
+        if ((float)h_gate[q] - ray > c->ray_margin) mark[q] = 1;
+      }
+    }
+    for (int64_t q = 0; q < W2; ++q)
+      if (mark[q] && na[q] == 0 && s->valid[q]) {
+        s->valid[q] = 0;
+        ++g_last_cleared;
+      }
+    free(mark);
+    free(line);
+    free(h_gate);
+    free(valid_gate);
+    free(acc_cell);
+    free(acc_z);
+  }
+
   if (c->time_var != 0.0f)
     for (int64_t j = 0; j < W2; ++j)
       if (s->valid[j]) s->var[j] = store_round(c, ORC_F32, s->var[j] + (double)c->time_var);
@@ -413,15 +527,10 @@ int64_t orc_fuse_image(const orc_cfg *c, orc_state *s, int32_t H, int32_t Wi, in
   }
   float fx = (float)K[0], fy = (float)K[1], cx = (float)K[2], cy = (float)K[3];
   float res = (float)c->res;
-  float half = (float)(W / 2);
   /* camera cell (clamped to the map) and camera height */
-  float cxm = (float)d[0], cym = (float)d[1], hc = (float)d[2];
-  float qx = floorf(cxm / res), qy = floorf(cym / res);
-  if (!(qx >= -half)) qx = -half;
-  if (!(qx <= half - 1.0f)) qx = half - 1.0f;
-  if (!(qy >= -half)) qy = -half;
-  if (!(qy <= half - 1.0f)) qy = half - 1.0f;
-  int32_t sx = (int32_t)qx + W / 2, sy = (int32_t)qy + W / 2;
+  float hc = (float)d[2];
+  int32_t sx, sy;
+  clamped_cell(c, (float)d[0], (float)d[1], &sx, &sy);
   /* decide every cell against the heights before this image */
   double *h0 = malloc((size_t)W2 * sizeof(double));
   for (int64_t j = 0; j < W2; ++j) h0[j] = s->h[j];

@@ -48,6 +48,16 @@ typedef struct {
   double w[ORC_MAX_LAYERS];         /* exponential-averaging weight                    */
   double var_meas[ORC_MAX_LAYERS];  /* Gaussian rule: known observation variance       */
   double alpha0[ORC_MAX_LAYERS];    /* Dirichlet rule: prior concentration per class   */
+  /* drift compensation (Table I "drift compensation"): 0 = off; else the valid heights move
+     by drift_alpha times the mean height error of the gate-accepted points in valid cells,
+     when at least drift_min_points such points exist */
+  double drift_alpha;
+  int32_t drift_min_points;
+  /* ray-cast clean-up (Table I "height update & ray cast"): 1 = on; a valid cell that a
+     gate-accepted point's sensor ray passes more than ray_margin below, and that accepts no
+     point of the call, becomes invalid */
+  int32_t ray_cleanup;
+  float ray_margin;
 } orc_cfg;
 
 /* Map state; every array is owned by the caller (W*W cells, or W*W*S values
@@ -80,6 +90,9 @@ int orc_point_cell(const orc_cfg *c, const float Rt[12], const float p[3], int32
 int64_t orc_fuse_points(const orc_cfg *c, orc_state *s, int64_t n, const float *xyz, int32_t n_src,
                         const orc_src *src, const double T[16], uint8_t *near_gate,
                         int32_t *cell_out);
+/* Diagnostics of the last orc_fuse_points call on this thread: drift shift applied (m),
+   number of points that entered the mean error, cells cleared by the ray cast. */
+void orc_last_fuse_info(double *drift, int64_t *drift_points, int64_t *cleared);
 void orc_move(const orc_cfg *c, orc_state *s, const double robot_xy[2]);
 int32_t orc_bresenham(int32_t sx, int32_t sy, int32_t ex, int32_t ey, int32_t *xy, int32_t cap);
 int64_t orc_fuse_image(const orc_cfg *c, orc_state *s, int32_t H, int32_t Wi, int32_t n_src,

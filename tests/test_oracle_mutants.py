@@ -13,7 +13,8 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 ORACLE = os.path.join(ROOT, "oracle")
 PINS = [os.path.join(ROOT, "tests", "test_oracle_points.py"),
-        os.path.join(ROOT, "tests", "test_oracle_image_move.py")]
+        os.path.join(ROOT, "tests", "test_oracle_image_move.py"),
+        os.path.join(ROOT, "tests", "test_oracle_raycast_drift.py")]
 
 # name -> [(exact source text, replacement)], each text occurring once in mem_oracle.c
 MUTANTS = {
@@ -49,6 +50,9 @@ MUTANTS = {
     "time variance added to never-observed cells":
         [("if (s->valid[j]) s->var[j] = store_round(c, ORC_F32, s->var[j] + (double)c->time_var);",
           "s->var[j] = store_round(c, ORC_F32, s->var[j] + (double)c->time_var);")],
+    "time variance only on cells touched by the call":
+        [("if (s->valid[j]) s->var[j] = store_round(c, ORC_F32, s->var[j] + (double)c->time_var);",
+          "if (s->valid[j] && np[j]) s->var[j] = store_round(c, ORC_F32, s->var[j] + (double)c->time_var);")],
     "exponential average blends a never-observed cell":
         [("double t = s->obs[l][j] ? c->w[l] * a + (1.0 - c->w[l]) * th[j * C + k] : a;",
           "double t = c->w[l] * a + (1.0 - c->w[l]) * th[j * C + k];")],
@@ -65,7 +69,8 @@ MUTANTS = {
     "map edge off by one": [("if (!(qx >= -half && qx < half && qy >= -half && qy < half)) return 0;",
                              "if (!(qx >= -half && qx <= half && qy >= -half && qy < half)) return 0;")],
     "visibility walk includes the target cell": [("for (int32_t m = 1; m + 1 < n; ++m) {", "for (int32_t m = 1; m < n; ++m) {")],
-    "ray parameter not normalised": [("float tq = (float)num / (float)den;", "float tq = (float)num;")],
+    "ray parameter not normalised": [("        float tq = (float)num / (float)den;\n        float ray = fmaf(tq, hz - hc, hc);",
+                                      "        float tq = (float)num;\n        float ray = fmaf(tq, hz - hc, hc);")],
     "image rule counts two observations per pixel":
         [("apply_rule(c, s, src[qs].layers[b], j, 1.0, S, S);", "apply_rule(c, s, src[qs].layers[b], j, 2.0, S, S);")],
     "invalid cells occlude": [("        if (!s->valid[q]) continue;\n        int32_t num", "        int32_t num")],
@@ -78,6 +83,33 @@ MUTANTS = {
           "        if (y > 0) s += h[j - W], ++m;\n        if (y + 1 < H) s += h[j + W], ++m;\n        h[j] = s / m;",
           "        if (x > 0) s += h[j - 1];\n        if (x + 1 < W) s += h[j + 1];\n"
           "        if (y > 0) s += h[j - W];\n        if (y + 1 < H) s += h[j + W];\n        h[j] = s / 4;")],
+    # drift compensation and ray-cast clean-up (Table I rows "drift compensation", "height
+    # update & ray cast")
+    "drift counts the gate's outliers":
+        [("      if (d * d > lam2 * ((float)s->var[j] + vm)) continue;\n      esum", "      esum")],
+    "drift counts points in invalid cells":
+        [("      if (!s->valid[j]) continue;\n      float d = z - (float)s->h[j];", "      float d = z - (float)s->h[j];")],
+    "drift moves the map the wrong way": [("s->h[j] = store_round(c, ORC_F32, s->h[j] + drift);",
+                                           "s->h[j] = store_round(c, ORC_F32, s->h[j] - drift);")],
+    "drift threshold off by one": [("drift_n >= c->drift_min_points", "drift_n > c->drift_min_points")],
+    "drift error summed, not averaged": [("c->drift_alpha * (esum / (double)drift_n)", "c->drift_alpha * esum")],
+    "drift ignores alpha": [("c->drift_alpha * (esum / (double)drift_n)", "(esum / (double)drift_n)")],
+    "ray ends at the cell's stored height instead of the point":
+        [("float ray = fmaf(tq, acc_z[a] - zs, zs);", "float ray = fmaf(tq, (float)h_gate[acc_cell[a]] - zs, zs);")],
+    "ray slope with the wrong sign": [("float ray = fmaf(tq, acc_z[a] - zs, zs);", "float ray = fmaf(tq, zs - acc_z[a], zs);")],
+    "clean-up clears cells that accepted a point":
+        [("if (mark[q] && na[q] == 0 && s->valid[q]) {", "if (mark[q] && s->valid[q]) {")],
+    "clean-up walk includes the sensor's cell":
+        [("      for (int32_t m = 1; m + 1 < nl; ++m) {\n        int32_t qx", "      for (int32_t m = 0; m + 1 < nl; ++m) {\n        int32_t qx")],
+    "clean-up margin ignored": [("if ((float)h_gate[q] - ray > c->ray_margin) mark[q] = 1;",
+                                 "if ((float)h_gate[q] - ray > 0.0f) mark[q] = 1;")],
+    "rejected points cast rays too":
+        [("    if (rej) {\n      ++nr[j];\n", "    if (rej) {\n      ++nr[j];\n      if (c->ray_cleanup) {\n"
+          "        acc_cell[n_accpt] = j;\n        acc_z[n_accpt] = z;\n        ++n_accpt;\n      }\n")],
+    "clean-up ray parameter not normalised": [("        float tq = (float)num / (float)den;\n        float ray = fmaf(tq, acc_z[a] - zs, zs);",
+                                               "        float tq = (float)num;\n        float ray = fmaf(tq, acc_z[a] - zs, zs);")],
+    "clean-up ray parameter along x only": [("int32_t num = (qx - sx) * dxs + (qy - sy) * dys;\n        float tq",
+                                             "int32_t num = (qx - sx) * dxs;\n        float tq")],
 }
 
 

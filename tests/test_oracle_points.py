@@ -203,8 +203,36 @@ def test_outlier_and_time_variance():
     m.fuse_points(np.array([[0.2, 0.2, 2.0]] * 2, np.float32), ident((0, 0, 1.0)))
     assert m.n_rej[j] == 2
     assert m.var[j] == pytest.approx(v1 + 2 * 0.5 + 0.25, rel=1e-12)
-    # a far valid cell that is not touched still ages by time_var
     assert m.valid.sum() == 1
+
+
+def test_time_variance_ages_untouched_valid_cells():
+    """time_var is added to EVERY valid cell once per call, touched or not (the height
+    update's process noise; the paper defers the model to its predecessor, this is the reading
+    stated in the design notes). Two valid cells; later calls touch only one of them, and an
+    empty cloud touches none: the other cell's variance grows by exactly time_var per call."""
+    p = mk(W=8, res=0.5, time_var=0.25)
+    m = O.OracleMap(p, round_store=False)
+    j, k = 4 * 8 + 4, 6 * 8 + 6
+    # first call: three readings in j and two in k (points below a sensor at height 1)
+    pts = np.array([[0.2, 0.2, -1.0]] * 3 + [[1.2, 1.2, -1.0]] * 2, np.float32)
+    m.fuse_points(pts, ident((0, 0, 1.0)))
+    assert m.valid[j] == 1 and m.valid[k] == 1 and m.valid.sum() == 2
+    s2 = lambda r: (0.01 + 0.002 * r) ** 2
+    vk = s2(math.sqrt(1.2 ** 2 * 2 + 1.0)) / 2 + 0.25      # fresh cell: s^2 / 2, then aged once
+    assert m.var[k] == pytest.approx(vk, rel=1e-6)   # float32 measurement variance
+    vk = m.var[k]
+    for call in range(3):
+        m.fuse_points(np.array([[0.2, 0.2, -1.0]], np.float32), ident((0, 0, 1.0)))
+        vk += 0.25
+        assert m.var[k] == pytest.approx(vk, rel=1e-12), f"untouched cell, call {call}"
+        assert m.n_acc[k] == 2
+    # an empty cloud ages both valid cells and nothing else
+    vj = m.var[j]
+    m.fuse_points(np.zeros((0, 3), np.float32), ident((0, 0, 1.0)))
+    assert m.var[k] == pytest.approx(vk + 0.25, rel=1e-12)
+    assert m.var[j] == pytest.approx(vj + 0.25, rel=1e-12)
+    assert m.valid.sum() == 2 and np.all(m.var[m.valid == 0] == 0)
 
 
 # --------------------------------------------------------------------------- fusion rules
