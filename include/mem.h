@@ -111,6 +111,27 @@ typedef struct {
   float range_min, range_max;
   float z_near;      /* camera near plane (m)                              */
   int64_t max_points; /* initial point capacity of the per-call scratch    */
+  /* Drift compensation (Table I "drift compensation"; the step is defined in
+   * the predecessor paper, this is the library's reading): 0 = off. Else,
+   * before the height update, the mean height error z - h of the points
+   * whose cell is valid and whose outlier gate accepts them (against the
+   * state before the call) is taken per map; when at least drift_min_points
+   * points enter it, every valid height of that map moves by
+   * float32(drift_alpha * mean), so the map follows the new cloud and the
+   * height update gates against the moved map. */
+  double drift_alpha;
+  int32_t drift_min_points;
+  /* Ray-cast clean-up (the "ray cast" of Table I's "height update & ray
+   * cast"; the library's reading of the predecessor's step): 1 = on. Every
+   * point its cell's gate accepts casts the ray from the sensor (the pose's
+   * translation; its cell clamped into the map) to the point along the
+   * Bresenham line of cells, both ends excluded; an intermediate cell that
+   * was valid and whose height exceeds the ray height there by more than
+   * ray_margin (m) is passed below, and if it accepted no point of the call
+   * it becomes invalid (stale obstacle removed). Runs after the height
+   * update, before the time variance. */
+  int32_t ray_cleanup;
+  float ray_margin;
 } mem_map_config;
 
 /* One input source: a row of `channels` values per point (point clouds) or
@@ -271,6 +292,12 @@ mem_status mem_get_profile(mem_map *m, double ms[MEM_PROFILE_SLOTS], int64_t cal
  * sorted points, touched cells, kept points, radix passes} of the last point
  * fuse (host output). */
 mem_status mem_get_stats(mem_map *m, void *stream, int64_t out[4]);
+/* Synchronise `stream`; out (host) = {drift shift applied to map map_index
+ * by the last point fuse (m, 0 when off or too few points), points that
+ * entered its mean error, cells of all maps invalidated by the last call's
+ * ray-cast clean-up}. Table I rows "drift compensation" and "height update &
+ * ray cast"; see mem_map_config. MEM_ERR_ARG for a bad index. */
+mem_status mem_get_drift(mem_map *m, int32_t map_index, void *stream, double out[3]);
 
 /* Diffusion (harmonic) inpainting of a batch of map crops, the fallback of the
  * learned inpainting and the reference it is judged against: each unknown
@@ -337,7 +364,8 @@ mem_status mem_unet_check(mem_unet *u, void *stream);
  * MEM_NOALLOC_MAX_POINTS points (about 22 MB, held by every GPU that loads
  * the library until the process exits); the call's parameters reach the
  * device as kernel arguments.
- *   cfg       host; n_maps must be 1 and n_layers 0; max_points is ignored
+ *   cfg       host; n_maps must be 1, n_layers 0, drift_alpha 0 and
+ *             ray_cleanup 0; max_points is ignored
  *   origin_xy host; world xy of the map centre (cell W/2 lower corner)
  *   n         points, 0 <= n <= MEM_NOALLOC_MAX_POINTS (larger: MEM_ERR_ARG)
  *   xyz       device float32 [n][3], sensor frame

@@ -243,6 +243,9 @@ cudaError_t alloc_scratch(Map* m, int64_t cap) {
   A(vals0, u32, cap + 4);
   A(vals1, u32, cap + 4);
   A(lookback, u32, 4 * tiles * 1024);
+  if (md.drift_alpha != 0.0) {
+    A(perr, float, cap + 4);
+  }
 #undef A
   md.cap = cap;
   md.cap_tiles = tiles;
@@ -369,6 +372,11 @@ static mem_status check_cfg(const mem_map_config* c) {
     if (L.rule == MEM_RULE_GAUSS && !(L.var_meas > 0.f)) return fail(MEM_ERR_ARG, "layer %d: var_meas > 0", l);
     if (L.rule == MEM_RULE_DIRICHLET && !(L.alpha0 > 0.f)) return fail(MEM_ERR_ARG, "layer %d: alpha0 > 0", l);
   }
+  if (!isfinite(c->drift_alpha)) return fail(MEM_ERR_ARG, "drift_alpha must be finite");
+  if (c->drift_min_points < 0) return fail(MEM_ERR_ARG, "drift_min_points must be >= 0");
+  if (c->ray_cleanup != 0 && c->ray_cleanup != 1) return fail(MEM_ERR_ARG, "ray_cleanup must be 0 or 1");
+  if (c->ray_cleanup && !(c->ray_margin >= 0.f && isfinite(c->ray_margin)))
+    return fail(MEM_ERR_ARG, "ray_margin must be finite and >= 0");
   return MEM_OK;
 }
 
@@ -399,6 +407,10 @@ extern "C" mem_status mem_create_map(const mem_map_config* cfg, mem_map** out) {
   md.range_max = cfg->range_max;
   md.z_near = cfg->z_near;
   md.n_layers = cfg->n_layers;
+  md.drift_alpha = cfg->drift_alpha;
+  md.drift_min = cfg->drift_min_points;
+  md.ray_on = cfg->ray_cleanup;
+  md.ray_margin = cfg->ray_margin;
   const int64_t cells = (int64_t)cfg->n_maps * md.W2;
   cudaError_t e = cudaSuccess;
   void* p = nullptr;
@@ -446,6 +458,14 @@ extern "C" mem_status mem_create_map(const mem_map_config* cfg, mem_map** out) {
   ALLOC(md.hist, uint32_t, 4 * 1024 + 16, "alloc hist");
   md.counters = md.hist + 4 * 1024;
   ALLOC(md.err, int, 2, "alloc err");  // [0] error word, [1] fault injection
+  ALLOC(md.dpart, double, (int64_t)cfg->n_maps * memk::kDriftR * 2, "alloc drift partials");
+  ALLOC(md.drift_out, float, 2 * (int64_t)cfg->n_maps, "alloc drift record");
+  if (md.ray_on) {
+    ALLOC(md.zacc, memk::u64, cells, "alloc clean-up stamps");
+    if ((e = cudaMemset(md.zacc, 0, sizeof(memk::u64) * (size_t)cells)) != cudaSuccess) return bail(e, "memset");
+  }
+  if ((e = cudaMemset(md.drift_out, 0, sizeof(float) * 2 * (size_t)cfg->n_maps)) != cudaSuccess)
+    return bail(e, "memset");
 #undef ALLOC
   e = alloc_scratch(m, cfg->max_points > 0 ? cfg->max_points : (1 << 20));
   if (e != cudaSuccess) return bail(e, "alloc scratch");
@@ -674,6 +694,8 @@ static mem_status run_points(Map* m, int nm, const int64_t* offsets, int64_t n, 
   MapCall* mcs = (MapCall*)(h + sizeof(PointJob));
   int64_t* offs = (int64_t*)(h + sizeof(PointJob) + sizeof(MapCall) * nm);
   job->n = n;
+  if (++m->call_id == 0) m->call_id = 1;  // 0 marks "never stamped"
+  job->call_id = m->call_id;
   job->xyz = xyz;
   job->n_maps = nm;
   job->n_src = n_src;
@@ -711,6 +733,9 @@ static mem_status run_points(Map* m, int nm, const int64_t* offsets, int64_t n, 
     CK(cudaStreamWaitEvent(st, ready, 0), "job upload wait");
   }
   if (n == 0) {  // no points: only the time-dependent variance growth of the valid cells
+    // (the call's statistics and drift record read as zero)
+    CK(cudaMemsetAsync(m->md.counters, 0, sizeof(uint32_t) * 16, st), "clear counters");
+    CK(cudaMemsetAsync(m->md.drift_out, 0, sizeof(float) * 2 * (size_t)nm, st), "clear drift record");
     CK(launch_time_update(m, st), "time update launch");
     return MEM_OK;
   }
@@ -1049,6 +1074,23 @@ extern "C" mem_status mem_get_stats(mem_map* mm, void* stream, int64_t out[4]) {
   out[1] = c[5];
   out[2] = c[6];
   out[3] = m->passes;
+  return MEM_OK;
+}
+
+extern "C" mem_status mem_get_drift(mem_map* mm, int32_t map_index, void* stream, double out[3]) {
+  if (!mm || !out) return fail(MEM_ERR_ARG, "NULL argument");
+  Map* m = &mm->m;
+  if (map_index < 0 || map_index >= m->cfg.n_maps) return fail(MEM_ERR_ARG, "map_index out of range");
+  CK(cudaStreamSynchronize((cudaStream_t)stream), "stream synchronize");
+  float d[2];
+  uint32_t c[16];
+  CK(cudaMemcpy(d, m->md.drift_out + 2 * map_index, sizeof(d), cudaMemcpyDeviceToHost), "read drift record");
+  CK(cudaMemcpy(c, m->md.counters, sizeof(c), cudaMemcpyDeviceToHost), "read counters");
+  uint32_t cnt;
+  memcpy(&cnt, &d[1], 4);
+  out[0] = d[0];
+  out[1] = (double)cnt;
+  out[2] = (double)c[10];
   return MEM_OK;
 }
 

@@ -22,6 +22,7 @@ struct Map {
   Tuning tune;
   int passes = 1;
   int key_bits = 1;
+  uint32_t call_id = 0;  // point-path calls so far (the clean-up's per-cell stamps)
   int n_sm = 148;
   int device = 0;
   std::vector<double> origin;  // [n_maps][2] world xy of each map centre
@@ -60,7 +61,7 @@ struct Map {
 
 // profile slots
 enum { kProfKey = 0, kProfDigits, kProfSort, kProfUnused3, kProfFuseTiles, kProfFuseCross,
-       kProfTime, kProfImage, kProfMove, kProfSlots };
+       kProfTime, kProfImage, kProfMove, kProfDrift, kProfRay, kProfSlots };
 
 // Brackets a launch group with events when profiling is on.
 struct ProfScope {

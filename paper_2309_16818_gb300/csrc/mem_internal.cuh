@@ -64,13 +64,24 @@ struct MapDev {
   u32* hist;        // [passes][radix] digit counts, then exclusive offsets
   u32* lookback;    // [passes][tiles][radix]
   u32* counters;    // [0..3] tile counters per pass, [4] crossing cells, [5] touched cells,
-                    // [6] kept points, [7] [9] tile counters of the fuse kernels, [8] slots
+                    // [6] kept points, [7] [9] tile counters of the fuse kernels, [8] slots,
+                    // [10] cells invalidated by the ray-cast clean-up
   float* partial;   // fuse scratch: tile slot bases, tile run counts, slots of acc words
   int64_t partial_cap;  // floats
   int* err;         // [0] device error word (bounded wait ran out), [1] fault injection for tests
   int64_t cap;      // point capacity of the scratch
   int64_t cap_tiles;
+  // drift compensation (drift_alpha != 0) and ray-cast clean-up (ray_on)
+  double drift_alpha;
+  int drift_min;
+  int ray_on;
+  float ray_margin;
+  float* perr;      // [cap] per point: z - h if it enters the mean height error, else NaN
+  double* dpart;    // [n_maps][kDriftR][2] partial sums and counts of the errors
+  float* drift_out; // [n_maps][2] shift applied, points in the mean (as float bits of a u32)
+  u64* zacc;        // [n_maps * W2] (call id << 32) | ~ordered(lowest accepted z of the call)
 };
+constexpr int kDriftR = 32;  // blocks per map of the drift reduction
 
 // Per-map, per-call parameters.
 struct MapCall {
@@ -124,6 +135,7 @@ struct FuseTables {
 // kernel sequence can be replayed from a CUDA graph.
 struct PointJob {
   int64_t n;
+  u32 call_id;  // increases by one per point-path call of a map object (never 0)
   const float* xyz;
   const int64_t* offsets;  // [n_maps + 1] or nullptr for one map
   const MapCall* maps;     // [n_maps]
@@ -301,6 +313,23 @@ __device__ __forceinline__ float layer_init(const LayerDev& L, int k) {
   if (L.rule == MEM_RULE_DIRICHLET) return L.alpha0;
   if (L.rule == MEM_RULE_CLASSMAX && k == 0) return -1.f;
   return 0.f;
+}
+
+// float -> u32 with the same order (negative values reversed), and back
+__host__ __device__ __forceinline__ u32 ordered_bits(u32 u) { return (u & 0x80000000u) ? ~u : (u | 0x80000000u); }
+__host__ __device__ __forceinline__ u32 unordered_bits(u32 o) { return (o & 0x80000000u) ? (o & 0x7fffffffu) : ~o; }
+
+// the cell of a map-frame position, clamped into the map (the sensor's cell of
+// a clean-up ray, the camera's cell of a visibility walk)
+__device__ __forceinline__ void clamped_cell(const MapDev& md, float px, float py, int& cx, int& cy) {
+  const float half = (float)(md.W / 2);
+  float qx = floorf(__fdiv_rn(px, md.res)), qy = floorf(__fdiv_rn(py, md.res));
+  if (!(qx >= -half)) qx = -half;
+  if (!(qx <= half - 1.0f)) qx = half - 1.0f;
+  if (!(qy >= -half)) qy = -half;
+  if (!(qy <= half - 1.0f)) qy = half - 1.0f;
+  cx = (int)qx + md.W / 2;
+  cy = (int)qy + md.W / 2;
 }
 
 // relaxed device-scope loads/stores for the radix-sort look-back

@@ -100,6 +100,8 @@ extern "C" mem_status mem_fuse_pointcloud_noalloc(const mem_map_config* cfg, con
     return memh::api_fail(MEM_ERR_ARG, "NULL argument");
   if (cfg->n_maps != 1 || cfg->n_layers != 0)
     return memh::api_fail(MEM_ERR_ARG, "the allocation-free fuse takes one map with no multi-modal layers");
+  if (cfg->drift_alpha != 0.0 || cfg->ray_cleanup != 0)
+    return memh::api_fail(MEM_ERR_ARG, "the allocation-free fuse runs without drift compensation and ray-cast clean-up");
   if (cfg->W < 2 || cfg->W > 16384 || (cfg->W & 1)) return memh::api_fail(MEM_ERR_ARG, "W must be even in [2, 16384]");
   if (!(cfg->res > 0.0)) return memh::api_fail(MEM_ERR_ARG, "res must be > 0");
   if (!(cfg->range_min <= cfg->range_max)) return memh::api_fail(MEM_ERR_ARG, "range_min > range_max");
@@ -121,6 +123,7 @@ extern "C" mem_status mem_fuse_pointcloud_noalloc(const mem_map_config* cfg, con
   m.cfg = *cfg;
   m.n_sm = n_sm;
   MapDev& md = m.md;
+  memset(&md, 0, sizeof(md));  // drift compensation and clean-up off, their buffers absent
   md.W = cfg->W;
   md.n_maps = 1;
   md.W2 = (u32)cfg->W * (u32)cfg->W;

@@ -66,6 +66,7 @@ __global__ void __launch_bounds__(256) k_points_key(MapDev md, const PointJob* _
   int cur_b = 0;
   u32 kept = 0, dropped = 0;
   const int lane = threadIdx.x & 31;
+  const bool drift = md.drift_alpha != 0.0;
   for (int64_t q = gtid; q < n4; q += gstride) {
     const int64_t i0 = q * 4;
     float p[12];
@@ -80,10 +81,12 @@ __global__ void __launch_bounds__(256) k_points_key(MapDev md, const PointJob* _
       for (int k = 0; k < 12; ++k) p[k] = (i0 + k / 3 < n) ? __ldg(xyz + i0 * 3 + k) : 0.f;
     }
     u32 keys[4];
+    float pe[4];  // drift compensation: z - h of a point that enters the mean height error, else NaN
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const int64_t i = i0 + k;
       keys[k] = md.sentinel;
+      pe[k] = __int_as_float(0x7fc00000);
       if (i >= n) continue;
       int b = 0;
       if (nm > 1) {
@@ -96,6 +99,11 @@ __global__ void __launch_bounds__(256) k_points_key(MapDev md, const PointJob* _
       PointEval e = eval_point(md, mc, p[3 * k], p[3 * k + 1], p[3 * k + 2]);
       const u32 key = e.keep ? (u32)b * md.W2 + phys_cell(md, mc, e.ix, e.iy) : md.sentinel;
       keys[k] = key;
+      if (drift && e.keep && (md.flags[key] & kFlagValid)) {
+        // the z error count: a point of a valid cell that the gate accepts (pre-call state)
+        const float h = md.h[key];
+        if (!gate_reject(e.z, h, md.var[key], e.vm, md.lam2)) pe[k] = __fsub_rn(e.z, h);
+      }
       kept += e.keep ? 1u : 0u;
       dropped += e.keep ? 0u : 1u;
     }
@@ -106,9 +114,13 @@ __global__ void __launch_bounds__(256) k_points_key(MapDev md, const PointJob* _
         for (int ps = 0; ps < passes; ++ps) atomicAdd(&shist[ps * RADIX + ((keys[k] >> (ps * RB)) & (RADIX - 1))], 1u);
     if (i0 + 4 <= n) {
       *reinterpret_cast<uint4*>(md.keys0 + i0) = make_uint4(keys[0], keys[1], keys[2], keys[3]);
+      if (drift) *reinterpret_cast<float4*>(md.perr + i0) = make_float4(pe[0], pe[1], pe[2], pe[3]);
     } else {
       for (int k = 0; k < 4; ++k)
-        if (i0 + k < n) md.keys0[i0 + k] = keys[k];
+        if (i0 + k < n) {
+          md.keys0[i0 + k] = keys[k];
+          if (drift) md.perr[i0 + k] = pe[k];
+        }
     }
   }
 #pragma unroll
@@ -123,6 +135,78 @@ __global__ void __launch_bounds__(256) k_points_key(MapDev md, const PointJob* _
   for (int i = threadIdx.x; i < passes * RADIX; i += blockDim.x)
     if (shist[i]) atomicAdd(&md.hist[i], shist[i]);
   if (threadIdx.x == 0 && shist[passes * RADIX]) atomicAdd(&md.counters[6], shist[passes * RADIX]);
+}
+
+// 2. drift compensation: per map, the mean of the height errors of the points
+//    that enter it (fixed assignment of points to threads and a fixed reduction
+//    tree, in float64), then every valid height of the map moves by
+//    float32(alpha * mean) when enough points entered it
+
+__global__ void __launch_bounds__(256) k_drift_reduce(MapDev md, const PointJob* __restrict__ job) {
+  if (*(volatile int*)md.err) return;  // a device error is pending: the point path does nothing
+  const int b = blockIdx.y, r = blockIdx.x;
+  int64_t o0 = 0, o1 = job->n;
+  if (job->offsets) {
+    o0 = job->offsets[b];
+    o1 = job->offsets[b + 1];
+  }
+  const int64_t len = o1 - o0;
+  const int64_t c0 = o0 + len * r / kDriftR, c1 = o0 + len * (r + 1) / kDriftR;
+  double sum = 0.0, cnt = 0.0;
+  for (int64_t i = c0 + threadIdx.x; i < c1; i += blockDim.x) {
+    const float e = md.perr[i];
+    if (!isnan(e)) {
+      sum += (double)e;
+      cnt += 1.0;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  }
+  __shared__ double ws[8][2];
+  const int warp = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    ws[warp][0] = sum;
+    ws[warp][1] = cnt;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double S = 0.0, Cn = 0.0;
+    for (int w = 0; w < 8; ++w) {
+      S += ws[w][0];
+      Cn += ws[w][1];
+    }
+    md.dpart[((int64_t)b * kDriftR + r) * 2] = S;
+    md.dpart[((int64_t)b * kDriftR + r) * 2 + 1] = Cn;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_drift_apply(MapDev md) {
+  if (*(volatile int*)md.err) return;  // a device error is pending: the point path does nothing
+  const int b = blockIdx.y;
+  __shared__ float s_shift;
+  if (threadIdx.x == 0) {
+    double S = 0.0, Cn = 0.0;
+    for (int r = 0; r < kDriftR; ++r) {
+      S += md.dpart[((int64_t)b * kDriftR + r) * 2];
+      Cn += md.dpart[((int64_t)b * kDriftR + r) * 2 + 1];
+    }
+    float shift = 0.f;
+    if (Cn > 0.0 && Cn >= (double)md.drift_min) shift = (float)(md.drift_alpha * (S / Cn));
+    s_shift = shift;
+    if (blockIdx.x == 0) {
+      md.drift_out[2 * b] = shift;
+      md.drift_out[2 * b + 1] = __uint_as_float((u32)Cn);
+    }
+  }
+  __syncthreads();
+  const float shift = s_shift;
+  if (shift == 0.f) return;
+  const int64_t base = (int64_t)b * md.W2;
+  for (u32 j = blockIdx.x * blockDim.x + threadIdx.x; j < md.W2; j += gridDim.x * blockDim.x)
+    if (md.flags[base + j] & kFlagValid) md.h[base + j] = __fadd_rn(md.h[base + j], shift);
 }
 
 // 3. one stable radix pass (onesweep: tiles taken in order from a counter,
@@ -759,6 +843,8 @@ __global__ void __launch_bounds__(kFT, 6) k_fuse_tiles(MapDev md, const PointJob
   const bool any_gauss = ft->any_gauss;  // Gaussian variances are written after every rule read them
   const float* __restrict__ xyz = job->xyz;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const bool ray = md.ray_on != 0;
+  const u64 call_hi = (u64)job->call_id << 32;
   // the call's tables (built on the host) into shared memory
   if (t < n_src) s.src[t] = job->src[t];
   if (t < md.n_layers) s.L[t] = md.L[t];
@@ -919,6 +1005,7 @@ __global__ void __launch_bounds__(kFT, 6) k_fuse_tiles(MapDev md, const PointJob
         }
       }
       __syncthreads();
+      u64 zk = 0;  // ray-cast clean-up: (call id, lowest z) key of an accepted point
       if (r0 == 0 && t < np) {
         // outlier gate against the pre-call state: height sums of the point
         const int r = s.pinf[t] >> 1;
@@ -932,6 +1019,21 @@ __global__ void __launch_bounds__(kFT, 6) k_fuse_tiles(MapDev md, const PointJob
         row[1] = rej ? 0.f : z * w;
         row[2] = rej ? 0.f : 1.f;
         row[3] = rej ? 1.f : 0.f;
+        if (!rej) zk = call_hi | (u64)(~ordered_bits(__float_as_uint(z)));
+      }
+      if (ray && r0 == 0) {
+        // the lowest accepted z of every cell: a segmented max of the keys over each warp's
+        // points (runs are contiguous), one atomic per run piece of the warp
+        const int run = t < np ? s.pinf[t] >> 1 : -1;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const u64 ok = __shfl_up_sync(0xffffffffu, zk, o);
+          const int orun = __shfl_up_sync(0xffffffffu, run, o);
+          if (lane >= o && orun == run && ok > zk) zk = ok;
+        }
+        const int nrun = __shfl_down_sync(0xffffffffu, run, 1);
+        if (t < np && zk != 0 && (lane == 31 || t == np - 1 || nrun != run))
+          atomicMax((unsigned long long*)(md.zacc + s.key[t + 1]), (unsigned long long)zk);
       }
       // per-point arg-max of a source whose channels began in an earlier round
       for (int c = 0; c < nr && s.fallback; ++c) {
@@ -1233,6 +1335,63 @@ __global__ void __launch_bounds__(128) k_fuse_cross(MapDev md, const PointJob* _
   if (lane == 0 && crossing) atomicAdd(&md.counters[4], crossing);
 }
 
+// 5. ray-cast clean-up: every cell that accepted points in this call walks the
+//    Bresenham line from the sensor's cell to itself (both ends excluded) with
+//    the ray of its lowest accepted point, and invalidates every intermediate
+//    cell that is valid, accepted no point of the call and stands more than
+//    ray_margin above the ray. The lowest point's ray passes below every cell
+//    any other point of the cell passes below (the ray height grows with the
+//    point's z under round-to-nearest, t >= 0), so one walk per cell decides
+//    exactly what one walk per accepted point decides. The heights read here
+//    belong to cells without accepted points, which this call did not change;
+//    invalidation is idempotent, so the result does not depend on the order.
+__global__ void __launch_bounds__(256) k_raycast(MapDev md, const PointJob* __restrict__ job) {
+  if (*(volatile int*)md.err) return;  // a device error is pending: the point path does nothing
+  const int W = md.W;
+  const int ix = blockIdx.x * 16 + threadIdx.x, iy = blockIdx.y * 16 + threadIdx.y;
+  const int b = blockIdx.z;
+  __shared__ MapCall smc;
+  if (threadIdx.x == 0 && threadIdx.y == 0) smc = job->maps[b];
+  __syncthreads();
+  if (ix >= W || iy >= W) return;
+  const u32 call = job->call_id;
+  const u32 base = (u32)b * md.W2;
+  const u64 v = __ldg((const unsigned long long*)(md.zacc + base + phys_cell(md, smc, ix, iy)));
+  if ((u32)(v >> 32) != call) return;
+  const float z = __uint_as_float(unordered_bits(~(u32)v));
+  int sx, sy;
+  clamped_cell(md, smc.t[0], smc.t[1], sx, sy);
+  const float zs = smc.t[2];
+  const float dz = __fsub_rn(z, zs);
+  const int dx = abs(ix - sx), dy = -abs(iy - sy);
+  const int stx = sx < ix ? 1 : -1, sty = sy < iy ? 1 : -1;
+  const int dxs = ix - sx, dys = iy - sy;
+  const float den = (float)(dxs * dxs + dys * dys);
+  int err = dx + dy, x = sx, y = sy;
+  u32 cleared = 0;
+  while (!(x == ix && y == iy)) {
+    const int e2 = 2 * err;
+    if (e2 >= dy) {
+      err += dy;
+      x += stx;
+    }
+    if (e2 <= dx) {
+      err += dx;
+      y += sty;
+    }
+    if (x == ix && y == iy) break;
+    const u32 q = base + phys_cell(md, smc, x, y);
+    if (!(md.flags[q] & kFlagValid)) continue;
+    if ((u32)(__ldg((const unsigned long long*)(md.zacc + q)) >> 32) == call) continue;  // accepted a point
+    const int num = (x - sx) * dxs + (y - sy) * dys;
+    const float tq = __fdiv_rn((float)num, den);
+    const float rz = __fmaf_rn(tq, dz, zs);
+    if (__fsub_rn(__ldg(md.h + q), rz) > md.ray_margin)
+      cleared += (atomicAnd(md.flags + q, ~kFlagValid) & kFlagValid) ? 1u : 0u;
+  }
+  if (cleared) atomicAdd(&md.counters[10], cleared);
+}
+
 // time-dependent variance growth of every valid cell
 __global__ void k_time_update(MapDev md, int64_t cells) {
   if (*(volatile int*)md.err) return;  // a device error is pending: the point path does nothing
@@ -1302,6 +1461,12 @@ static cudaError_t launch_rb(Map* m, const PointJob* d_job, cudaStream_t st) {
     ProfScope ps(m, kProfKey, st);
     k_points_key<RB><<<sms * bps, 256, sizeof(u32) * (P * (1 << RB) + 1), st>>>(md, d_job, P);
   }
+  if (md.drift_alpha != 0.0) {
+    ProfScope ps(m, kProfDrift, st);
+    k_drift_reduce<<<dim3(kDriftR, md.n_maps), 256, 0, st>>>(md, d_job);
+    const u32 per_map = (md.W2 + 256 * 8 - 1) / (256 * 8);
+    k_drift_apply<<<dim3(per_map, md.n_maps), 256, 0, st>>>(md);
+  }
   {
     ProfScope ps(m, kProfSort, st);
     for (int p = 0; p < P; ++p) k_onesweep<RB><<<sms * 2, kSortThreads, sort_smem<RB>(), st>>>(md, d_job, p);
@@ -1314,6 +1479,10 @@ static cudaError_t launch_rb(Map* m, const PointJob* d_job, cudaStream_t st) {
   {
     ProfScope ps(m, kProfFuseCross, st);
     k_fuse_cross<<<sms * 8, 128, 0, st>>>(md, d_job);
+  }
+  if (md.ray_on) {
+    ProfScope ps(m, kProfRay, st);
+    k_raycast<<<dim3((md.W + 15) / 16, (md.W + 15) / 16, md.n_maps), dim3(16, 16), 0, st>>>(md, d_job);
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;

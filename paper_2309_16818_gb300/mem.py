@@ -31,7 +31,7 @@ EXPORTS = ["mem_create_map", "mem_destroy_map", "mem_move_map", "mem_fuse_pointc
            "mem_autotune_batch", "mem_inpaint_diffusion", "mem_unet_create", "mem_unet_destroy",
            "mem_unet_param_count", "mem_unet_set_params", "mem_unet_get_params", "mem_unet_forward",
            "mem_unet_gradients", "mem_unet_train_step", "mem_unet_check", "mem_inject_fault",
-           "mem_noalloc_check"]
+           "mem_noalloc_check", "mem_get_drift"]
 NOALLOC_MAX_POINTS = 1 << 18
 PROFILE_SLOTS = ["key", "digit_scan", "radix_sort", "unused3", "fuse_tiles", "fuse_cross",
                  "time_var", "image", "move"]
@@ -47,7 +47,9 @@ class MapConfig(C.Structure):
                 ("n_layers", C.c_int32), ("layers", LayerDesc * MAX_LAYERS),
                 ("sigma0", C.c_float), ("sigma1", C.c_float), ("gate_lambda", C.c_float),
                 ("outlier_var", C.c_float), ("time_var", C.c_float), ("range_min", C.c_float),
-                ("range_max", C.c_float), ("z_near", C.c_float), ("max_points", C.c_int64)]
+                ("range_max", C.c_float), ("z_near", C.c_float), ("max_points", C.c_int64),
+                ("drift_alpha", C.c_double), ("drift_min_points", C.c_int32),
+                ("ray_cleanup", C.c_int32), ("ray_margin", C.c_float)]
 
 
 class Source(C.Structure):
@@ -93,7 +95,7 @@ def lib():
             "mem_unet_gradients": [P, I32, I32, I32, P, P, P, P, I64, P, P, P],
             "mem_unet_train_step": [P, I32, I32, I32, P, P, P, P, I64, C.c_float, P, P],
             "mem_unet_check": [P, P], "mem_inject_fault": [P, I32],
-            "mem_noalloc_check": [P],
+            "mem_noalloc_check": [P], "mem_get_drift": [P, I32, P, P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -196,7 +198,8 @@ class Map:
     def __init__(self, W: int, res: float, layers=(), n_maps: int = 1, sigma0: float = 0.01,
                  sigma1: float = 0.002, gate_lambda: float = 2.0, outlier_var: float = 0.0,
                  time_var: float = 0.0, range_min: float = 0.1, range_max: float = 50.0,
-                 z_near: float = 0.05, max_points: int = 1 << 20):
+                 z_near: float = 0.05, max_points: int = 1 << 20, drift_alpha: float = 0.0,
+                 drift_min_points: int = 1, ray_cleanup: bool = False, ray_margin: float = 0.1):
         cfg = MapConfig()
         cfg.W, cfg.n_maps, cfg.res = W, n_maps, res
         self.layers = list(layers)
@@ -209,6 +212,8 @@ class Map:
         cfg.outlier_var, cfg.time_var = outlier_var, time_var
         cfg.range_min, cfg.range_max, cfg.z_near = range_min, range_max, z_near
         cfg.max_points = max_points
+        cfg.drift_alpha, cfg.drift_min_points = drift_alpha, drift_min_points
+        cfg.ray_cleanup, cfg.ray_margin = int(bool(ray_cleanup)), ray_margin
         self.cfg = cfg
         self.W, self.n_maps, self.res = W, n_maps, res
         self._h = C.c_void_p()
@@ -359,6 +364,13 @@ class Map:
         calls = np.zeros(16, np.int64)
         _ck(lib().mem_get_profile(self._h, ms.ctypes.data, calls.ctypes.data))
         return {k: (float(ms[i]), int(calls[i])) for i, k in enumerate(PROFILE_SLOTS)}
+
+    def get_drift(self, map_index=0, stream=None):
+        """{drift: shift applied by the last point fuse, drift_points: points in its mean,
+        cleared: cells invalidated by the last call's ray-cast clean-up}."""
+        out = np.zeros(3, np.float64)
+        _ck(lib().mem_get_drift(self._h, map_index, _stream(stream), out.ctypes.data))
+        return dict(drift=float(out[0]), drift_points=int(out[1]), cleared=int(out[2]))
 
     def get_stats(self, stream=None):
         out = np.zeros(4, np.int64)
