@@ -3,17 +3,39 @@
 TEST INFRASTRUCTURE ONLY: used by the test suite to check the CUDA training and inference
 kernels; nothing in the library imports it.
 
-The network (the paper only motivates "neural networks that take map layers as input"; this
-layout is the reading stated in the design notes): levels of widths c = (c1, c2, c3, c4); each
+The network (the paper only motivates neural networks that read map layers and produce a new
+layer; this layout is the reading stated in the design notes): levels of widths c = (c1, c2, c3, c4); each
 level two 3x3 convolutions (zero padding) with ReLU; 2x2 max-pooling between encoder levels;
 nearest-neighbour upsampling and channel concatenation [upsampled, skip] in the decoder; a
 final 1x1 convolution gives a residual added to the diffusion fill. Tensors are NHWC.
 Convolutions are written as im2col followed by a matrix product (the library matmul is the
 only primitive used).
+
+Storage rounding (optional, ``store=round_bf16``): a network run in BF16 keeps its activations
+and its activation gradients in BF16 between layers while every sum runs in a wider format.
+With ``store`` given, forward and backward round exactly the tensors such a run stores: each
+convolution's output after bias and ReLU, the 1x1 head's gradient into the last activation,
+every convolution's data gradient, the 2x2 sums of the upsampled part of a decoder input's
+gradient, and the sum of a skip gradient and a pooled gradient. Weights, inputs, weight and
+bias gradients and the loss are left to the caller (the weights and inputs are rounded before
+the call when they are stored in BF16). Without ``store`` every value stays float64.
 """
 from __future__ import annotations
 
 import numpy as np
+
+
+def round_bf16(x):
+    """float64 -> nearest bfloat16 value (ties to even), as float64: the value is rounded to
+    float32 first, then its low 16 bits are rounded away."""
+    f = np.ascontiguousarray(np.asarray(x, np.float64).astype(np.float32))
+    u = f.view(np.uint32).astype(np.uint64)
+    u = ((u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)
+    return u.view(np.float32).astype(np.float64).reshape(np.shape(x))
+
+
+def _keep(x):
+    return x
 
 
 def layer_shapes(cin: int, widths):
@@ -100,14 +122,16 @@ def upsample_backward(dy):
     return dy.reshape(N, H // 2, 2, W // 2, 2, C).sum(axis=(2, 4))
 
 
-def forward(p, x, widths):
-    """x: [N,H,W,Cin] -> residual [N,H,W] and the activations the backward pass needs."""
+def forward(p, x, widths, store=None):
+    """x: [N,H,W,Cin] -> residual [N,H,W] and the activations the backward pass needs.
+    store: rounding applied to every stored activation (see the module notes)."""
+    store = store or _keep
     convs, _ = layer_shapes(x.shape[3], widths)
     a = {"in": x}
 
     def cr(name, t):
         y = conv3x3(t, p[name + ".w"], p[name + ".b"])
-        r = np.maximum(y, 0.0)
+        r = store(np.maximum(y, 0.0))
         a[name + ".in"] = t
         a[name + ".out"] = r
         return r
@@ -131,20 +155,30 @@ def loss_and_grad_out(res, fill, target, hidden):
     return float((diff ** 2).sum() / cnt), 2.0 * diff / cnt
 
 
-def backward(p, a, dres, widths):
-    """Gradients of every parameter given d loss / d residual [N,H,W]."""
+def backward(p, a, dres, widths, store=None, trace=None):
+    """Gradients of every parameter given d loss / d residual [N,H,W]. store: rounding applied
+    to every stored activation gradient (see the module notes); trace (a dict, optional)
+    receives each of those stored gradients under a name."""
+    store = store or _keep
     g = {}
+
+    def keep(name, t):
+        t = store(t)
+        if trace is not None:
+            trace[name] = t
+        return t
+
     d1 = a["d1"]
     do = dres[..., None]
     g["out.w"] = d1.reshape(-1, d1.shape[3]).T @ do.reshape(-1, 1)
     g["out.b"] = np.array([do.sum()])
-    dt = do @ p["out.w"].T
+    dt = keep("head", do @ p["out.w"].T)
 
     def crb(name, dt):
         dt = dt * (a[name + ".out"] > 0)
         dx, dw, db = conv3x3_backward(a[name + ".in"], p[name + ".w"], dt)
         g[name + ".w"], g[name + ".b"] = dw, db
-        return dx
+        return keep(name + ".dx", dx)
 
     def split(dcat, c_up):
         return dcat[..., :c_up], dcat[..., c_up:]
@@ -152,15 +186,15 @@ def backward(p, a, dres, widths):
     c1, c2, c3, c4 = widths
     dcat = crb("d1a", crb("d1b", dt))
     du, de1 = split(dcat, c2)
-    dcat = crb("d2a", crb("d2b", upsample_backward(du)))
+    dcat = crb("d2a", crb("d2b", keep("up2", upsample_backward(du))))
     du, de2 = split(dcat, c3)
-    dcat = crb("d3a", crb("d3b", upsample_backward(du)))
+    dcat = crb("d3a", crb("d3b", keep("up3", upsample_backward(du))))
     du, de3 = split(dcat, c4)
-    de4 = crb("e4a", crb("e4b", upsample_backward(du)))
-    de3 = de3 + maxpool_backward(a["e3"], de4)
+    de4 = crb("e4a", crb("e4b", keep("up4", upsample_backward(du))))
+    de3 = keep("skip3", de3 + maxpool_backward(a["e3"], de4))
     de3 = crb("e3a", crb("e3b", de3))
-    de2 = de2 + maxpool_backward(a["e2"], de3)
+    de2 = keep("skip2", de2 + maxpool_backward(a["e2"], de3))
     de2 = crb("e2a", crb("e2b", de2))
-    de1 = de1 + maxpool_backward(a["e1"], de2)
+    de1 = keep("skip1", de1 + maxpool_backward(a["e1"], de2))
     crb("e1a", crb("e1b", de1))
     return g

@@ -170,6 +170,11 @@ UNET_MUTANTS = {
                                                 "return float((diff ** 2).sum()), 2.0 * diff / cnt"),
     "hidden mask ignored in the loss": ("diff = (fill + res - target) * hidden", "diff = (fill + res - target)"),
     "decoder split at the skip width": ("du, de1 = split(dcat, c2)", "du, de1 = split(dcat, c1)"),
+    "storage rounding skips the decoder input gradient": ('keep("up2", upsample_backward(du))', "upsample_backward(du)"),
+    "storage rounding skips the activations": ("r = store(np.maximum(y, 0.0))", "r = np.maximum(y, 0.0)"),
+    "storage rounding skips the skip sums": ('de2 = keep("skip2", de2 + maxpool_backward(a["e2"], de3))',
+                                             'de2 = de2 + maxpool_backward(a["e2"], de3)'),
+    "bf16 rounding truncates": ("u = ((u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000)", "u = ((u) & 0xFFFF0000)"),
 }
 
 _RUN_UNET = r'''

@@ -104,3 +104,60 @@ def test_loss_counts_hidden_cells_only():
     assert loss == pytest.approx((d ** 2).sum() / 3, rel=1e-12)
     assert np.all(g[hidden == 0] == 0)
     np.testing.assert_allclose(g[hidden == 1], 2 * d / 3, rtol=1e-12)
+
+
+# --------------------------------------------------------------------------- storage rounding
+
+def test_round_bf16_values_and_ties():
+    """Nearest bfloat16, ties to even: 1 + 2^-8 lies halfway between 1 and 1 + 2^-7 and goes
+    to 1 (even); 1 + 3 * 2^-8 goes to 1 + 2^-6; exact bf16 values, signs, zero stay."""
+    v = np.array([1 + 2 ** -8, 1 + 3 * 2 ** -8, 1 + 2 ** -7, -3.0, 0.0, 1 + 2 ** -9, 1 + 2 ** -8 + 2 ** -20])
+    exp = np.array([1.0, 1 + 2 ** -6, 1 + 2 ** -7, -3.0, 0.0, 1.0, 1 + 2 ** -7])
+    assert np.array_equal(U.round_bf16(v), exp)
+
+
+def _bf16_exact(t):
+    return np.array_equal(U.round_bf16(t), t)
+
+
+def test_storage_rounding_rounds_every_stored_tensor():
+    """With store=round_bf16 every activation and every stored activation gradient is a bf16
+    value, and the stored gradients are the ones a BF16 run keeps: the head's gradient, each
+    convolution's data gradient, the three upsampled-gradient sums and the three skip sums."""
+    p, x, fill, target, hidden = _setup(seed=4)
+    for k in p:
+        if k.endswith(".w") and k != "out.w":
+            p[k] = U.round_bf16(p[k])
+    x = U.round_bf16(x)
+    res, a = U.forward(p, x, WIDTHS, store=U.round_bf16)
+    for k, t in a.items():
+        if k.endswith(".out") or k in ("e1", "e2", "e3", "e4", "d3", "d2", "d1"):
+            assert _bf16_exact(t), k
+    _, dres = U.loss_and_grad_out(res, fill, target, hidden)
+    tr = {}
+    U.backward(p, a, dres, WIDTHS, store=U.round_bf16, trace=tr)
+    convs, _ = U.layer_shapes(3, WIDTHS)
+    names = {"head", "up2", "up3", "up4", "skip1", "skip2", "skip3"} | {n + ".dx" for n, _, _ in convs}
+    assert set(tr) == names
+    for k, t in tr.items():
+        assert _bf16_exact(t), k
+        assert np.abs(t).sum() > 0, k
+
+
+def test_storage_rounding_stays_near_the_exact_network():
+    """Rounding the stored tensors perturbs the result, but only as rounding can: the residual
+    within 2e-2 of float64 and every gradient pointing the same way (cosine > 0.9) -- a
+    rounding that flips a ReLU or a max-pool choice near a tie moves a far layer's gradient by
+    up to tens of per cent on a small network, so no tighter bound holds for every layer."""
+    p, x, fill, target, hidden = _setup(seed=5, H=32, W=32)
+    r0, a0 = U.forward(p, x, WIDTHS)
+    r1, a1 = U.forward(p, x, WIDTHS, store=U.round_bf16)
+    assert np.linalg.norm(r1 - r0) / np.linalg.norm(r0) < 2e-2
+    g0 = U.backward(p, a0, U.loss_and_grad_out(r0, fill, target, hidden)[1], WIDTHS)
+    g1 = U.backward(p, a1, U.loss_and_grad_out(r1, fill, target, hidden)[1], WIDTHS, store=U.round_bf16)
+    for k in g0:
+        a, b = g1[k].ravel(), g0[k].ravel()
+        assert (a @ b) / (np.linalg.norm(a) * np.linalg.norm(b)) > 0.9, k
+    # without store the result is the plain float64 network, bit for bit
+    r2, a2 = U.forward(p, x, WIDTHS, store=None)
+    assert np.array_equal(r2, r0)
