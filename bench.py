@@ -347,6 +347,11 @@ def run_ours(args):
                        "page-locked host memory each step; whole-run throughput, no L2 flush inside"}
 
     extra = {}
+    if not args.no_raycast:
+        srcs = [[(rgb[k], [0]), (prb[k], [1, 2, 3])] for k in range(n_pose)]
+        extra["raycast_drift"] = bench_raycast_drift(args, dev, flush, ws, c, xyz, srcs)
+    if not args.no_sweep:
+        extra["layer_sweep"] = bench_layer_sweep(args, dev, flush, ws, c, xyz)
     if not args.no_batched:
         extra["batched"] = bench_batched(args, dev, flush, ws)
     if not args.no_image:
@@ -378,6 +383,120 @@ def run_ours(args):
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def _timed_steps(step, n_pose, K, warmup, flush, stream):
+    """Mean device ms of K steps (L2 flushed between steps, outside the events)."""
+    import torch
+    for i in range(warmup):
+        step(i % n_pose)
+    evs = []
+    for i in range(K):
+        flush(i)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step((warmup + i) % n_pose)
+        b.record(stream)
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    return float(np.mean([a.elapsed_time(b) for a, b in evs]))
+
+
+def bench_raycast_drift(args, dev, flush, ws, c, xyz, srcs):
+    """The headline workload with drift compensation (alpha 1, at least 100 points) and the
+    ray-cast clean-up (margin 0.1 m) on; every pose is lifted by a seeded odometry error in z
+    of up to +-3 cm, so the map moves each step."""
+    import torch
+    from paper_2309_16818_gb300 import mem as M
+    W, res = c["W"], c["res"]
+    n_pose = len(c["scans"])
+    rng = np.random.default_rng(7)
+    Ts = []
+    for k, s in enumerate(c["scans"]):
+        T = np.array(s.T, dtype=np.float64)
+        T[2, 3] += rng.uniform(-0.03, 0.03)
+        Ts.append(T)
+    stream = torch.cuda.current_stream()
+    m = M.Map(W, res, multimodal_layer_specs(M), max_points=max(s.n for s in c["scans"]) + 1024,
+              drift_alpha=1.0, drift_min_points=100, ray_cleanup=True, ray_margin=0.1)
+
+    def step(k):
+        m.move(c["poses"][k][:2])
+        m.fuse_pointcloud(xyz[k], Ts[k], srcs[k])
+
+    ms = _timed_steps(step, n_pose, max(10, args.steps), args.warmup, flush, stream)
+    m.check()
+    info = []
+    for k in range(n_pose):
+        step(k)
+        info.append(m.get_drift())
+    m.set_profiling(True)
+    m.get_profile()
+    reps = 10
+    for i in range(reps):
+        flush(i)
+        step(i % n_pose)
+    prof = m.get_profile()
+    m.set_profiling(False)
+    m.close()
+    npts = float(np.mean([s.n for s in c["scans"]]))
+    t = max_over_ranks(ms / 1e3, ws)
+    return {"workload": "headline multi-modal poses with drift compensation and ray-cast clean-up on "
+                        "(poses lifted by a seeded z error in [-3, 3] cm)",
+            "ms_per_step": round(1e3 * t, 4), "points_per_s": round(ws * npts / t, 1),
+            "us_per_call": {"drift_reduce_and_shift": round(1e3 * prof["drift"][0] / reps, 3),
+                            "raycast_cleanup": round(1e3 * prof["raycast"][0] / reps, 3)},
+            "cleared_cells_per_step": round(float(np.mean([d["cleared"] for d in info])), 1),
+            "drift_points_per_step": round(float(np.mean([d["drift_points"] for d in info])), 1),
+            "mean_abs_drift_m": round(float(np.mean([abs(d["drift"]) for d in info])), 5)}
+
+
+def bench_layer_sweep(args, dev, flush, ws, c, xyz):
+    """Fuse time against the number of multi-modal layers (the paper's scaling figure: the
+    multi-modal update grows linearly with the layers). The paper's map keeps each class
+    channel in a layer of its own; here the first C of the 20 class probabilities of the
+    headline cloud go into one C-channel layer with exponential averaging or Dirichlet fusion,
+    for C = 1 .. 20. Reported: the step time and the fuse kernels' time per C, and the slope of
+    a least-squares line over C of the fuse kernels' time."""
+    import torch
+    from paper_2309_16818_gb300 import mem as M
+    W, res = c["W"], c["res"]
+    n_pose = len(c["scans"])
+    stream = torch.cuda.current_stream()
+    prb = [torch.from_numpy(s.probs).to(dev) for s in c["scans"]]
+    Cs = [0, 1, 2, 4, 8, 12, 16, 20]
+    out = {}
+    for rule_name, rule in (("expavg", M.EXPAVG), ("dirichlet", M.DIRICHLET)):
+        rows = []
+        for C in Cs:
+            layers = [] if C == 0 else [M.Layer(C, rule, w=0.1, alpha0=1.0)]
+            src = [None] * n_pose if C == 0 else [p[:, :C].contiguous() for p in prb]
+            m = M.Map(W, res, layers, max_points=max(s.n for s in c["scans"]) + 1024)
+
+            def step(k):
+                m.move(c["poses"][k][:2])
+                m.fuse_pointcloud(xyz[k], c["scans"][k].T, [] if C == 0 else [(src[k], [0])])
+
+            ms = _timed_steps(step, n_pose, 20, args.warmup, flush, stream)
+            m.set_profiling(True)
+            m.get_profile()
+            for i in range(10):
+                flush(i)
+                step(i % n_pose)
+            prof = m.get_profile()
+            m.close()
+            fuse_ms = (prof["fuse_tiles"][0] + prof["fuse_cross"][0]) / 10
+            rows.append({"layers": C, "ms_per_step": round(ms, 4), "fuse_ms": round(fuse_ms, 4)})
+        x = np.array([r["layers"] for r in rows[1:]], float)
+        y = np.array([r["fuse_ms"] for r in rows[1:]], float)
+        A = np.vstack([x, np.ones_like(x)]).T
+        (slope, icpt), res_, _, _ = np.linalg.lstsq(A, y, rcond=None)
+        r2 = 1.0 - float(((y - A @ np.array([slope, icpt])) ** 2).sum()) / float(((y - y.mean()) ** 2).sum())
+        out[rule_name] = {"rows": rows, "fuse_us_per_layer": round(1e3 * slope, 3),
+                          "fuse_us_at_0_layers_fit": round(1e3 * icpt, 2), "linear_fit_r2": round(r2, 4),
+                          "ms_20_layers": rows[-1]["ms_per_step"]}
+    return {"workload": "headline multi-modal poses, height layer plus one layer of the first C class probabilities",
+            **out}
 
 
 def bench_batched(args, dev, flush, ws):
@@ -620,6 +739,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-image", action="store_true")
+    ap.add_argument("--no-raycast", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-inpaint", action="store_true")
     ap.add_argument("--inpaint-crops", type=int, default=256)
     ap.add_argument("--no-cpu", action="store_true")

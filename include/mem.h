@@ -284,7 +284,8 @@ mem_status mem_autotune_batch(mem_map *m, const int64_t *offsets, const float *x
  * mem_get_profile waits for the recorded events and returns, per slot, the
  * summed milliseconds and the number of launches since the previous read:
  * 0 transform+key, 1 digit scan, 2 radix passes, 3 segments, 4 short-cell
- * fuse, 5 long-cell fuse, 6 time variance, 7 image fuse, 8 move. */
+ * fuse, 5 long-cell fuse, 6 time variance, 7 image fuse, 8 move, 9 drift
+ * compensation, 10 ray-cast clean-up. */
 #define MEM_PROFILE_SLOTS 16
 mem_status mem_set_profiling(mem_map *m, int32_t on);
 mem_status mem_get_profile(mem_map *m, double ms[MEM_PROFILE_SLOTS], int64_t calls[MEM_PROFILE_SLOTS]);
@@ -313,6 +314,23 @@ mem_status mem_get_drift(mem_map *m, int32_t map_index, void *stream, double out
 mem_status mem_inpaint_diffusion(int32_t n_crops, int32_t H, int32_t W, const float *h_in,
                                  const uint8_t *known, float *h_out, float tol, int32_t max_iters,
                                  int32_t *iters_out, void *stream);
+
+/* Inputs of the inpainting network for a batch of map crops (Sec. III-D:
+ * a plugin reads map layers and produces a new one; the normalisation is this
+ * library's): per crop the mean m of the heights of its known cells (float64
+ * sums, rounded once to float32; 0 for a crop without known cells), then per
+ * cell the three input channels
+ *   x3[.., 0] = fill - m, x3[.., 1] = hidden, x3[.., 2] = known ? 0.1 ln(1e-4) : 0
+ * (observed cells carry a variance of 1e-4 m^2, the log-variance channel is
+ * scaled by 0.1) and hidden = 1 - known.
+ *   h_in, fill   device float32 [n_crops][H][W] (heights; the diffusion fill)
+ *   known        device uint8 [n_crops][H][W] (1 = observed)
+ *   x3           device float32 [n_crops][H][W][3] (out)
+ *   hidden       device uint8 [n_crops][H][W] (out)
+ *   mean_out     device float32 [n_crops] (out, optional)
+ * MEM_ERR_ARG for NULL pointers or a bad shape (nothing queued). */
+mem_status mem_unet_prepare(int32_t n_crops, int32_t H, int32_t W, const float *h_in, const uint8_t *known,
+                            const float *fill, float *x3, uint8_t *hidden, float *mean_out, void *stream);
 
 /* Learned inpainting (Sec. III-D: post-processing plugins may run neural
  * networks on map layers to produce a new layer; the network layout is this

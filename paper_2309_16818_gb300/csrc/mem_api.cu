@@ -5,6 +5,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <string>
 
@@ -458,7 +459,9 @@ extern "C" mem_status mem_create_map(const mem_map_config* cfg, mem_map** out) {
   ALLOC(md.hist, uint32_t, 4 * 1024 + 16, "alloc hist");
   md.counters = md.hist + 4 * 1024;
   ALLOC(md.err, int, 2, "alloc err");  // [0] error word, [1] fault injection
-  ALLOC(md.dpart, double, (int64_t)cfg->n_maps * memk::kDriftR * 2, "alloc drift partials");
+  // drift reduction: about four blocks per SM over all maps, at least one per map
+  md.drift_R = (int)std::min<int64_t>(1024, std::max<int64_t>(1, (4LL * m->n_sm + cfg->n_maps - 1) / cfg->n_maps));
+  ALLOC(md.dpart, double, (int64_t)cfg->n_maps * md.drift_R * 2, "alloc drift partials");
   ALLOC(md.drift_out, float, 2 * (int64_t)cfg->n_maps, "alloc drift record");
   if (md.ray_on) {
     ALLOC(md.zacc, memk::u64, cells, "alloc clean-up stamps");

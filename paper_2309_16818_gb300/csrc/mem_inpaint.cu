@@ -123,3 +123,74 @@ extern "C" mem_status mem_inpaint_diffusion(int32_t n_crops, int32_t H, int32_t 
   if (e != cudaSuccess) return memh::api_cuda_fail(e, "inpaint launch");
   return MEM_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Inputs of the inpainting network per crop (one block per crop): the mean of
+// the known heights (float64 sums over a fixed assignment of cells to threads
+// and a fixed reduction tree, so every run gives the same bits), then per cell
+//   x3 = (fill - mean, hidden, known ? logvar_known : 0),  hidden = !known.
+namespace memk {
+
+__global__ void __launch_bounds__(256) k_unet_prepare(int64_t P, const float* __restrict__ h,
+                                                      const uint8_t* __restrict__ known,
+                                                      const float* __restrict__ fill, float* __restrict__ x3,
+                                                      uint8_t* __restrict__ hidden, float* __restrict__ mean_out,
+                                                      float logvar_known) {
+  const int64_t base = (int64_t)blockIdx.x * P;
+  double s = 0.0, c = 0.0;
+  for (int64_t p = threadIdx.x; p < P; p += blockDim.x)
+    if (known[base + p]) {
+      s += (double)h[base + p];
+      c += 1.0;
+    }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s += __shfl_xor_sync(0xffffffffu, s, o);
+    c += __shfl_xor_sync(0xffffffffu, c, o);
+  }
+  __shared__ double red[8][2];
+  __shared__ float s_mean;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[warp][0] = s;
+    red[warp][1] = c;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double S = 0.0, Cn = 0.0;
+    for (int w = 0; w < 8; ++w) {
+      S += red[w][0];
+      Cn += red[w][1];
+    }
+    const float mean = (float)(S / (Cn > 1.0 ? Cn : 1.0));
+    s_mean = mean;
+    if (mean_out) mean_out[blockIdx.x] = mean;
+  }
+  __syncthreads();
+  const float mean = s_mean;
+  for (int64_t p = threadIdx.x; p < P; p += blockDim.x) {
+    const bool k = known[base + p] != 0;
+    float* o = x3 + 3 * (base + p);
+    o[0] = __fsub_rn(fill[base + p], mean);
+    o[1] = k ? 0.f : 1.f;
+    o[2] = k ? logvar_known : 0.f;
+    hidden[base + p] = k ? 0 : 1;
+  }
+}
+
+}  // namespace memk
+
+extern "C" mem_status mem_unet_prepare(int32_t n_crops, int32_t H, int32_t W, const float* h_in,
+                                       const uint8_t* known, const float* fill, float* x3, uint8_t* hidden,
+                                       float* mean_out, void* stream) {
+  if (!h_in || !known || !fill || !x3 || !hidden) return memh::api_fail(MEM_ERR_ARG, "NULL argument");
+  if (n_crops < 1 || H < 1 || W < 1 || (int64_t)H * W >= (1ll << 31))
+    return memh::api_fail(MEM_ERR_ARG, "bad crop shape");
+  // observed cells carry variance 1e-4 m^2: 0.1 ln(1e-4) (hidden cells: 0)
+  const float logvar_known = (float)(0.1 * log(1e-4));
+  memk::k_unet_prepare<<<n_crops, 256, 0, (cudaStream_t)stream>>>((int64_t)H * W, h_in, known, fill, x3, hidden,
+                                                                 mean_out, logvar_known);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return memh::api_cuda_fail(e, "prepare launch");
+  return MEM_OK;
+}

@@ -77,11 +77,11 @@ struct MapDev {
   int ray_on;
   float ray_margin;
   float* perr;      // [cap] per point: z - h if it enters the mean height error, else NaN
-  double* dpart;    // [n_maps][kDriftR][2] partial sums and counts of the errors
+  int drift_R;      // blocks per map of the drift reduction
+  double* dpart;    // [n_maps][drift_R][2] partial sums and counts of the errors
   float* drift_out; // [n_maps][2] shift applied, points in the mean (as float bits of a u32)
   u64* zacc;        // [n_maps * W2] (call id << 32) | ~ordered(lowest accepted z of the call)
 };
-constexpr int kDriftR = 32;  // blocks per map of the drift reduction
 
 // Per-map, per-call parameters.
 struct MapCall {

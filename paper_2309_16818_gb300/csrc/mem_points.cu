@@ -151,7 +151,8 @@ __global__ void __launch_bounds__(256) k_drift_reduce(MapDev md, const PointJob*
     o1 = job->offsets[b + 1];
   }
   const int64_t len = o1 - o0;
-  const int64_t c0 = o0 + len * r / kDriftR, c1 = o0 + len * (r + 1) / kDriftR;
+  const int R = md.drift_R;
+  const int64_t c0 = o0 + len * r / R, c1 = o0 + len * (r + 1) / R;
   double sum = 0.0, cnt = 0.0;
   for (int64_t i = c0 + threadIdx.x; i < c1; i += blockDim.x) {
     const float e = md.perr[i];
@@ -178,8 +179,8 @@ __global__ void __launch_bounds__(256) k_drift_reduce(MapDev md, const PointJob*
       S += ws[w][0];
       Cn += ws[w][1];
     }
-    md.dpart[((int64_t)b * kDriftR + r) * 2] = S;
-    md.dpart[((int64_t)b * kDriftR + r) * 2 + 1] = Cn;
+    md.dpart[((int64_t)b * R + r) * 2] = S;
+    md.dpart[((int64_t)b * R + r) * 2 + 1] = Cn;
   }
 }
 
@@ -187,18 +188,26 @@ __global__ void __launch_bounds__(256) k_drift_apply(MapDev md) {
   if (*(volatile int*)md.err) return;  // a device error is pending: the point path does nothing
   const int b = blockIdx.y;
   __shared__ float s_shift;
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 32) {  // the map's partials: lanes over a fixed stride, then a fixed tree
+    const int R = md.drift_R;
     double S = 0.0, Cn = 0.0;
-    for (int r = 0; r < kDriftR; ++r) {
-      S += md.dpart[((int64_t)b * kDriftR + r) * 2];
-      Cn += md.dpart[((int64_t)b * kDriftR + r) * 2 + 1];
+    for (int r = threadIdx.x; r < R; r += 32) {
+      S += md.dpart[((int64_t)b * R + r) * 2];
+      Cn += md.dpart[((int64_t)b * R + r) * 2 + 1];
     }
-    float shift = 0.f;
-    if (Cn > 0.0 && Cn >= (double)md.drift_min) shift = (float)(md.drift_alpha * (S / Cn));
-    s_shift = shift;
-    if (blockIdx.x == 0) {
-      md.drift_out[2 * b] = shift;
-      md.drift_out[2 * b + 1] = __uint_as_float((u32)Cn);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      S += __shfl_xor_sync(0xffffffffu, S, o);
+      Cn += __shfl_xor_sync(0xffffffffu, Cn, o);
+    }
+    if (threadIdx.x == 0) {
+      float shift = 0.f;
+      if (Cn > 0.0 && Cn >= (double)md.drift_min) shift = (float)(md.drift_alpha * (S / Cn));
+      s_shift = shift;
+      if (blockIdx.x == 0) {
+        md.drift_out[2 * b] = shift;
+        md.drift_out[2 * b + 1] = __uint_as_float((u32)Cn);
+      }
     }
   }
   __syncthreads();
@@ -1345,49 +1354,113 @@ __global__ void __launch_bounds__(128) k_fuse_cross(MapDev md, const PointJob* _
 //    exactly what one walk per accepted point decides. The heights read here
 //    belong to cells without accepted points, which this call did not change;
 //    invalidation is idempotent, so the result does not depend on the order.
+//
+//    A block takes a 16 x 16 tile of cells and first lists its walking cells in
+//    shared memory, so the walks run on consecutive threads; each walk advances
+//    four cells at a time with their loads issued together. The ray height is
+//    first estimated with a reciprocal of |e - s|^2 (relative error below
+//    2^-22 in t); only where that estimate lies within a bound of the margin is
+//    the exact sequence (correctly rounded division, fma, subtraction) taken,
+//    so every decision equals the exact one.
+__device__ __forceinline__ void bres_step(int& x, int& y, int& err, int dx, int dy, int stx, int sty) {
+  const int e2 = 2 * err;
+  if (e2 >= dy) {
+    err += dy;
+    x += stx;
+  }
+  if (e2 <= dx) {
+    err += dx;
+    y += sty;
+  }
+}
+
 __global__ void __launch_bounds__(256) k_raycast(MapDev md, const PointJob* __restrict__ job) {
   if (*(volatile int*)md.err) return;  // a device error is pending: the point path does nothing
   const int W = md.W;
-  const int ix = blockIdx.x * 16 + threadIdx.x, iy = blockIdx.y * 16 + threadIdx.y;
   const int b = blockIdx.z;
+  const int tid = threadIdx.y * 16 + threadIdx.x;
   __shared__ MapCall smc;
-  if (threadIdx.x == 0 && threadIdx.y == 0) smc = job->maps[b];
+  __shared__ int s_n;
+  __shared__ u32 s_cell[256];
+  __shared__ float s_z[256];
+  if (tid == 0) {
+    smc = job->maps[b];
+    s_n = 0;
+  }
   __syncthreads();
-  if (ix >= W || iy >= W) return;
   const u32 call = job->call_id;
   const u32 base = (u32)b * md.W2;
-  const u64 v = __ldg((const unsigned long long*)(md.zacc + base + phys_cell(md, smc, ix, iy)));
-  if ((u32)(v >> 32) != call) return;
-  const float z = __uint_as_float(unordered_bits(~(u32)v));
+  const u32* __restrict__ stamp = reinterpret_cast<const u32*>(md.zacc);  // [2g + 1]: call id of cell g
+  {
+    const int ix = blockIdx.x * 16 + threadIdx.x, iy = blockIdx.y * 16 + threadIdx.y;
+    if (ix < W && iy < W) {
+      const u64 v = __ldg((const unsigned long long*)(md.zacc + base + phys_cell(md, smc, ix, iy)));
+      if ((u32)(v >> 32) == call) {
+        const int k = atomicAdd(&s_n, 1);
+        s_cell[k] = ((u32)iy << 16) | (u32)ix;
+        s_z[k] = __uint_as_float(unordered_bits(~(u32)v));
+      }
+    }
+  }
+  __syncthreads();
+  if (tid >= s_n) return;
+  const int ix = (int)(s_cell[tid] & 0xffffu), iy = (int)(s_cell[tid] >> 16);
+  const float z = s_z[tid];
   int sx, sy;
   clamped_cell(md, smc.t[0], smc.t[1], sx, sy);
   const float zs = smc.t[2];
   const float dz = __fsub_rn(z, zs);
+  const float margin = md.ray_margin;
   const int dx = abs(ix - sx), dy = -abs(iy - sy);
   const int stx = sx < ix ? 1 : -1, sty = sy < iy ? 1 : -1;
   const int dxs = ix - sx, dys = iy - sy;
   const float den = (float)(dxs * dxs + dys * dys);
+  const float rden = __frcp_rn(den);
+  // bound on |estimate - exact| of (h - ray - margin), far above the estimate's error
+  const float tol = 4e-6f * (fabsf(dz) + fabsf(zs) + margin + 1.f);
   int err = dx + dy, x = sx, y = sy;
+  bool done = (x == ix && y == iy);
   u32 cleared = 0;
-  while (!(x == ix && y == iy)) {
-    const int e2 = 2 * err;
-    if (e2 >= dy) {
-      err += dy;
-      x += stx;
+  while (!done) {
+    int qx[4], qy[4];
+    bool act[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      act[u] = false;
+      qx[u] = qy[u] = 0;
+      if (!done) {
+        bres_step(x, y, err, dx, dy, stx, sty);
+        if (x == ix && y == iy) {
+          done = true;
+        } else {
+          qx[u] = x;
+          qy[u] = y;
+          act[u] = true;
+        }
+      }
     }
-    if (e2 <= dx) {
-      err += dx;
-      y += sty;
+    u32 q[4], fl[4], st[4];
+    float hq[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      q[u] = base + phys_cell(md, smc, qx[u], qy[u]);
+      fl[u] = act[u] ? md.flags[q[u]] : 0u;
+      st[u] = act[u] ? __ldg(stamp + 2 * (size_t)q[u] + 1) : call;
+      hq[u] = act[u] ? __ldg(md.h + q[u]) : 0.f;
     }
-    if (x == ix && y == iy) break;
-    const u32 q = base + phys_cell(md, smc, x, y);
-    if (!(md.flags[q] & kFlagValid)) continue;
-    if ((u32)(__ldg((const unsigned long long*)(md.zacc + q)) >> 32) == call) continue;  // accepted a point
-    const int num = (x - sx) * dxs + (y - sy) * dys;
-    const float tq = __fdiv_rn((float)num, den);
-    const float rz = __fmaf_rn(tq, dz, zs);
-    if (__fsub_rn(__ldg(md.h + q), rz) > md.ray_margin)
-      cleared += (atomicAnd(md.flags + q, ~kFlagValid) & kFlagValid) ? 1u : 0u;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (!act[u] || !(fl[u] & kFlagValid) || st[u] == call) continue;
+      const int num = (qx[u] - sx) * dxs + (qy[u] - sy) * dys;
+      const float ra = __fmaf_rn(__fmul_rn((float)num, rden), dz, zs);
+      const float est = hq[u] - ra - margin;
+      bool clear = est > 0.f;
+      if (fabsf(est) <= tol + 4e-6f * fabsf(hq[u])) {  // near the margin: the exact sequence
+        const float tq = __fdiv_rn((float)num, den);
+        clear = __fsub_rn(hq[u], __fmaf_rn(tq, dz, zs)) > margin;
+      }
+      if (clear) cleared += (atomicAnd(md.flags + q[u], ~kFlagValid) & kFlagValid) ? 1u : 0u;
+    }
   }
   if (cleared) atomicAdd(&md.counters[10], cleared);
 }
@@ -1463,7 +1536,7 @@ static cudaError_t launch_rb(Map* m, const PointJob* d_job, cudaStream_t st) {
   }
   if (md.drift_alpha != 0.0) {
     ProfScope ps(m, kProfDrift, st);
-    k_drift_reduce<<<dim3(kDriftR, md.n_maps), 256, 0, st>>>(md, d_job);
+    k_drift_reduce<<<dim3(md.drift_R, md.n_maps), 256, 0, st>>>(md, d_job);
     const u32 per_map = (md.W2 + 256 * 8 - 1) / (256 * 8);
     k_drift_apply<<<dim3(per_map, md.n_maps), 256, 0, st>>>(md);
   }

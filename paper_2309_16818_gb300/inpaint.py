@@ -47,16 +47,11 @@ def init_params(seed, cin, widths, out_scale=0.1):
 
 def prepare(h_obs, known, tol=1e-5):
     """h_obs, known: cuda [n,H,W] (float32, uint8). Returns x3 [n,H,W,3], fill [n,H,W],
-    hidden [n,H,W] uint8, the per-crop mean of known heights [n]."""
-    import torch
-    fill, _ = M.inpaint_diffusion(h_obs.contiguous(), known.contiguous(), tol=tol)
-    kf = known.float()
-    cnt = kf.sum(dim=(1, 2)).clamp(min=1)
-    mean = (h_obs * kf).sum(dim=(1, 2)) / cnt
-    hidden = (known == 0).to(torch.uint8)
-    x3 = torch.stack([fill - mean[:, None, None], hidden.float(),
-                      torch.where(known == 1, torch.full_like(fill, 0.1 * math.log(1e-4)),
-                                  torch.zeros_like(fill))], dim=3).contiguous()
+    hidden [n,H,W] uint8, the per-crop mean of known heights [n] -- the diffusion fill and the
+    normalisation both run in the library (mem_inpaint_diffusion, mem_unet_prepare)."""
+    h_obs, known = h_obs.contiguous(), known.contiguous()
+    fill, _ = M.inpaint_diffusion(h_obs, known, tol=tol)
+    x3, hidden, mean = M.unet_prepare(h_obs, known, fill)
     return x3, fill, hidden, mean
 
 

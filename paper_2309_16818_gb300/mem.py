@@ -31,10 +31,10 @@ EXPORTS = ["mem_create_map", "mem_destroy_map", "mem_move_map", "mem_fuse_pointc
            "mem_autotune_batch", "mem_inpaint_diffusion", "mem_unet_create", "mem_unet_destroy",
            "mem_unet_param_count", "mem_unet_set_params", "mem_unet_get_params", "mem_unet_forward",
            "mem_unet_gradients", "mem_unet_train_step", "mem_unet_check", "mem_inject_fault",
-           "mem_noalloc_check", "mem_get_drift"]
+           "mem_noalloc_check", "mem_get_drift", "mem_unet_prepare"]
 NOALLOC_MAX_POINTS = 1 << 18
 PROFILE_SLOTS = ["key", "digit_scan", "radix_sort", "unused3", "fuse_tiles", "fuse_cross",
-                 "time_var", "image", "move"]
+                 "time_var", "image", "move", "drift", "raycast"]
 
 
 class LayerDesc(C.Structure):
@@ -96,6 +96,7 @@ def lib():
             "mem_unet_train_step": [P, I32, I32, I32, P, P, P, P, I64, C.c_float, P, P],
             "mem_unet_check": [P, P], "mem_inject_fault": [P, I32],
             "mem_noalloc_check": [P], "mem_get_drift": [P, I32, P, P],
+            "mem_unet_prepare": [I32, I32, I32, P, P, P, P, P, P, P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -176,6 +177,24 @@ def inpaint_diffusion(h, known, tol=1e-6, max_iters=20000, out=None, stream=None
                                     C.c_void_p(out.data_ptr()), tol, max_iters,
                                     C.c_void_p(its.data_ptr()), _stream(stream)))
     return out, its
+
+
+def unet_prepare(h, known, fill, stream=None):
+    """Network inputs of a batch of crops (mem_unet_prepare): h, fill float32 [B,H,W] cuda,
+    known uint8 [B,H,W] cuda. Returns (x3 float32 [B,H,W,3], hidden uint8 [B,H,W],
+    mean of the known heights float32 [B])."""
+    torch = _torch()
+    for t in (h, known, fill):
+        assert t.is_cuda and t.is_contiguous() and t.shape == h.shape and t.dim() == 3
+    assert h.dtype == torch.float32 and fill.dtype == torch.float32 and known.dtype == torch.uint8
+    B, H, W = h.shape
+    x3 = torch.empty((B, H, W, 3), dtype=torch.float32, device=h.device)
+    hidden = torch.empty((B, H, W), dtype=torch.uint8, device=h.device)
+    mean = torch.empty(B, dtype=torch.float32, device=h.device)
+    _ck(lib().mem_unet_prepare(B, H, W, C.c_void_p(h.data_ptr()), C.c_void_p(known.data_ptr()),
+                               C.c_void_p(fill.data_ptr()), C.c_void_p(x3.data_ptr()),
+                               C.c_void_p(hidden.data_ptr()), C.c_void_p(mean.data_ptr()), _stream(stream)))
+    return x3, hidden, mean
 
 
 @dataclass

@@ -37,52 +37,83 @@ def _cos(a, b):
     return float((a * b).sum() / (np.linalg.norm(a) * np.linalg.norm(b) + 1e-30))
 
 
-@pytest.mark.parametrize("H,W", [(32, 32), (32, 24)])
-def test_forward_and_gradients_match_float64_oracle(torch, H, W):
+def _gpu_and_oracle(torch, widths, N, H, W, seed):
+    """Forward pass, loss and gradients of the library and of the float64 oracle (plain and
+    with the library's bf16 storage rounding) on the same bf16-rounded weights and inputs."""
     from paper_2309_16818_gb300 import mem as M
     from paper_2309_16818_gb300.inpaint import init_params
-    rng = np.random.default_rng(0)
-    N = 2
-    flat = init_params(1, 3, WIDTHS, out_scale=1.0)
+    rng = np.random.default_rng(seed)
+    flat = init_params(1, 3, widths, out_scale=1.0)
     x3 = rng.normal(size=(N, H, W, 3)).astype(np.float32)
     fill = rng.normal(size=(N, H, W)).astype(np.float32)
     target = rng.normal(size=(N, H, W)).astype(np.float32)
     hidden = (rng.random((N, H, W)) < 0.5).astype(np.uint8)
-    net = M.UNet(3, WIDTHS)
+    net = M.UNet(3, widths)
     net.set_params(torch.from_numpy(flat).cuda())
     tx = torch.from_numpy(x3).cuda()
     tf = torch.from_numpy(fill).cuda()
     pred = net.forward(tx, tf).cpu().numpy()
     g, loss = net.gradients(tx, tf, torch.from_numpy(target).cuda(), torch.from_numpy(hidden).cuda())
-    g = g.cpu().numpy()
-    # oracle on the same (bf16-rounded) weights and inputs, everything else in float64
-    p = _unflatten(flat, 3, WIDTHS)
+    net.check()
+    g = _unflatten(g.cpu().numpy(), 3, widths)
+    p = _unflatten(flat, 3, widths)
     for k in p:
         if k.endswith(".w") and k != "out.w":
             p[k] = _bf16(p[k])
-    res, acts = U.forward(p, _bf16(x3), WIDTHS)
-    lo, dres = U.loss_and_grad_out(res, fill.astype(np.float64), target, hidden.astype(np.float64))
-    go = U.backward(p, acts, dres, WIDTHS)
-    # forward: bf16 activations between 14 layers -> a few parts in a thousand of the residual
-    err = np.linalg.norm(pred - (fill + res)) / np.linalg.norm(res)
-    assert err < 2e-2, err
-    assert abs(float(loss.item()) - lo) <= 2e-2 * lo
-    # gradients: activations and gradients are stored in bf16 (2^-9 relative rounding) along a
-    # path of up to 28 roundings, and a rounding can flip a ReLU or a max-pool choice near a
-    # tie, which reroutes a gradient; with random weights the layers farthest from the loss
-    # (and the bottleneck biases, summed over only a few pixels) reach 0.1-0.15 relative
-    gg = _unflatten(g, 3, WIDTHS)
-    worst = []
+    out = {}
+    noise = np.random.default_rng(seed + 100)
+
+    def jitter(t):
+        # the oracle's own sensitivity: each stored value moved by float32-sized relative noise
+        # (what float32 instead of float64 accumulation does) before its bf16 rounding
+        return U.round_bf16(t * (1.0 + noise.normal(0.0, 3e-7, np.shape(t))))
+
+    modes = [("f64", None), ("bf16", U.round_bf16)] + [(f"bf16_jitter{k}", jitter) for k in range(4)]
+    for mode, store in modes:
+        res, acts = U.forward(p, _bf16(x3), widths, store=store)
+        lo, dres = U.loss_and_grad_out(res, fill.astype(np.float64), target, hidden.astype(np.float64))
+        out[mode] = (res, lo, U.backward(p, acts, dres, widths, store=store))
+    return pred, fill, float(loss.item()), g, out
+
+
+def _grad_errors(g, go):
+    rows = []
     for name in go:
-        a, b = gg[name].ravel(), go[name].ravel()
-        c = _cos(a, b)
-        rel = np.linalg.norm(a - b) / (np.linalg.norm(b) + 1e-30)
-        worst.append((rel, c, name))
-        assert c > 0.98 and rel < 0.2, (name, c, rel)
-    # the layers next to the loss are much closer
-    for rel, c, name in worst:
-        if name.startswith(("out", "d1b")):
-            assert rel < 0.03, (name, rel)
+        a, b = g[name].ravel(), go[name].ravel()
+        rows.append((name, np.linalg.norm(a - b) / (np.linalg.norm(b) + 1e-30), _cos(a, b)))
+    return rows
+
+
+@pytest.mark.parametrize("widths,H,W", [((32, 32, 32, 32), 32, 32), ((32, 32, 32, 32), 32, 24),
+                                        ((32, 64, 128, 128), 32, 32)])
+def test_forward_and_gradients_match_oracle(torch, widths, H, W):
+    """Against the oracle with the library's storage rounding (activations and activation
+    gradients rounded to bf16 where the library stores them): the residual within 1e-2, and
+    every parameter's gradient within 2e-2 relative or at cosine >= 0.999 -- unless the oracle
+    itself moves further than that when its stored values are jittered by float32-sized noise
+    before rounding (a value near a bf16 rounding boundary or a max-pool tie lands on the other
+    side; a sum with heavy cancellation, like the first layer's weight gradient here, turns
+    that into several per cent): then within 3 times that floor (the largest move over four
+    jitter draws). Against the plain float64
+    oracle the forward pass stays within 2e-2 (bf16 activations between 14 layers)."""
+    pred, fill, loss, g, out = _gpu_and_oracle(torch, widths, 2, H, W, seed=0)
+    res64, lo64, _ = out["f64"]
+    res, lo, go = out["bf16"]
+    jit = [out[k][2] for k in out if k.startswith("bf16_jitter")]
+    assert np.linalg.norm(pred - (fill + res64)) / np.linalg.norm(res64) < 2e-2
+    err = np.linalg.norm(pred - (fill + res)) / np.linalg.norm(res)
+    assert err < 1e-2, err
+    assert abs(loss - lo) <= 1e-2 * lo
+    floor = {}  # the largest move over four jitter draws
+    for gj in jit:
+        for n, rel, _ in _grad_errors(gj, go):
+            floor[n] = max(floor.get(n, 0.0), rel)
+    bad = [(n, rel, c, floor[n]) for n, rel, c in _grad_errors(g, go)
+           if not (rel <= 2e-2 or c >= 0.999 or (floor[n] > 2e-2 and rel <= 3 * floor[n]))]
+    assert not bad, bad
+    within_r12 = sum(1 for n, rel, c in _grad_errors(g, go) if rel <= 2e-2 or c >= 0.999)
+    print(f"\n{widths} {H}x{W}: {within_r12}/{len(go)} parameters within rel 2e-2 or cos 0.999; "
+          f"floors above 2e-2: { {n: round(v, 3) for n, v in floor.items() if v > 2e-2} }")
 
 
 def test_forward_at_crop_size_with_several_tiles_per_block(torch):
@@ -151,3 +182,30 @@ def test_training_beats_diffusion_fill(torch, capsys):
         print(f"\ntraining losses {['%.2e' % x for x in losses]}")
         print(f"held-out RMSE on hidden cells: U-Net {r_net:.4f} m, diffusion {r_dif:.4f} m")
     assert np.isfinite(r_net) and r_net < r_dif
+
+
+def test_prepare_matches_numpy_restatement(torch):
+    """mem_unet_prepare against the network-input normalisation written out in NumPy: per crop
+    the float64 mean of the known heights rounded to float32 (0 without known cells), then
+    x3 = (fill - mean, hidden, known ? 0.1 ln(1e-4) : 0) and hidden = 1 - known; crops with
+    no known cell and with every cell known included."""
+    from paper_2309_16818_gb300 import mem as M
+    gt, kn = synth.inpaint_crops(6, size=64, seed=9)
+    kn = kn.copy()
+    kn[4] = 0
+    kn[5] = 1
+    rng = np.random.default_rng(2)
+    h = np.where(kn == 1, gt, 0.0).astype(np.float32)
+    fill = (gt + rng.normal(0, 0.05, gt.shape)).astype(np.float32)
+    x3, hid, mean = M.unet_prepare(torch.from_numpy(h).cuda(), torch.from_numpy(kn).cuda(),
+                                   torch.from_numpy(fill).cuda())
+    x3, hid, mean = x3.cpu().numpy(), hid.cpu().numpy(), mean.cpu().numpy()
+    for b in range(len(h)):
+        k = kn[b] == 1
+        m = np.float32(h[b][k].astype(np.float64).sum() / max(1, int(k.sum())))
+        assert abs(mean[b] - m) <= np.spacing(np.abs(m)), (b, mean[b], m)
+        assert np.allclose(x3[b, ..., 0], fill[b] - mean[b], rtol=0, atol=0)
+        assert np.array_equal(x3[b, ..., 1], (~k).astype(np.float32))
+        assert np.array_equal(x3[b, ..., 2], np.where(k, np.float32(0.1 * np.log(1e-4)), np.float32(0.0)))
+        assert np.array_equal(hid[b], (~k).astype(np.uint8))
+    assert mean[4] == 0.0
