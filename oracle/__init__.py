@@ -75,7 +75,15 @@ class State(C.Structure):
 
 class Src(C.Structure):
     _fields_ = [("data", C.c_void_p), ("dtype", C.c_int32), ("channels", C.c_int32),
-                ("n_layers", C.c_int32), ("layers", C.c_int32 * MAX_SRC_LAYERS)]
+                ("n_layers", C.c_int32), ("layers", C.c_int32 * MAX_SRC_LAYERS), ("topk", C.c_int32)]
+
+
+@dataclass
+class TopK:
+    """Class probabilities given as the top k classes (Sec. III-C): ``pairs`` float32 [N, 2k] of
+    (class id, probability) per row, ``K`` the class count of the layers the source feeds."""
+    pairs: np.ndarray
+    K: int
 
 
 _lib = None
@@ -220,6 +228,17 @@ class OracleMap:
     def _sources(self, sources, keep):
         arr = (Src * max(1, len(sources)))()
         for i, (data, layers) in enumerate(sources):
+            if isinstance(data, TopK):
+                a = np.ascontiguousarray(data.pairs, dtype=np.float32)
+                keep.append(a)
+                arr[i].data = _p(a)
+                arr[i].dtype = F32
+                arr[i].channels = data.K
+                arr[i].topk = a.shape[-1] // 2
+                arr[i].n_layers = len(layers)
+                for k, l in enumerate(layers):
+                    arr[i].layers[k] = l
+                continue
             bf16 = isinstance(data, tuple)
             a = np.ascontiguousarray(data[0] if bf16 else data)
             keep.append(a)
@@ -233,7 +252,7 @@ class OracleMap:
 
     def fuse_points(self, xyz: np.ndarray, T: np.ndarray, sources=(), want_cells=False,
                     want_near=False):
-        """sources: list of (array [N,C] or (uint16 bf16 bits array,), [layer ids])."""
+        """sources: list of (array [N,C], (uint16 bf16 bits array,) or TopK, [layer ids])."""
         xyz = np.ascontiguousarray(xyz, dtype=np.float32)
         n = xyz.shape[0]
         keep = []

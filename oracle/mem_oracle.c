@@ -41,6 +41,15 @@ static double store_round(const orc_cfg *c, int fmt, double x) {
 }
 
 static double load_val(const orc_src *s, int64_t row, int k) {
+  if (s->topk > 0) { /* class k of a row of top-k (class id, probability) pairs */
+    const float *r = (const float *)s->data + row * 2 * (int64_t)s->topk;
+    float v = 0.0f;
+    for (int j = 0; j < s->topk; ++j) {
+      float id = r[2 * j];
+      if (id >= 0.0f && id < (float)s->channels && id == floorf(id) && (int)id == k) v += r[2 * j + 1];
+    }
+    return (double)v;
+  }
   int64_t off = row * (int64_t)s->channels + k;
   switch (s->dtype) {
     case ORC_F32: return (double)((const float *)s->data)[off];

@@ -74,13 +74,19 @@ typedef struct {
 } orc_state;
 
 /* One input source: a row of `channels` values per point (or per pixel, HWC)
- * fused into each of `layers`. */
+ * fused into each of `layers`. With topk > 0 (class probabilities given as the
+ * top k classes, Sec. III-C) a row is instead topk pairs (class id, probability)
+ * of float32 (dtype ORC_F32), and `channels` is the class count K: the point
+ * stands for the K-vector that holds each listed probability at its class (ids
+ * that are not whole numbers in [0, K) are ignored; a repeated id adds up, in
+ * float32, in row order) and zero elsewhere. */
 typedef struct {
   const void *data;
   int32_t dtype;
   int32_t channels;
   int32_t n_layers;
   int32_t layers[ORC_MAX_SRC_LAYERS];
+  int32_t topk;
 } orc_src;
 
 void orc_init_state(const orc_cfg *c, orc_state *s);

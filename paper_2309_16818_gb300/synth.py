@@ -135,6 +135,17 @@ def dirichlet_probs(rng, n: int, k: int, alpha: float) -> np.ndarray:
     return (g / g.sum(axis=1, keepdims=True)).astype(np.float32)
 
 
+def topk_pairs(probs: np.ndarray, k: int) -> np.ndarray:
+    """A segmentation output reduced to its k most probable classes per row: float32 [N, 2k] of
+    (class id, probability), largest first, the smaller class first on equal probabilities."""
+    p = np.asarray(probs, np.float32)
+    order = np.argsort(-p, axis=1, kind="stable")[:, :k]
+    out = np.empty((p.shape[0], 2 * k), np.float32)
+    out[:, 0::2] = order.astype(np.float32)
+    out[:, 1::2] = np.take_along_axis(p, order, axis=1)
+    return out
+
+
 def f32_to_bf16_bits(a: np.ndarray) -> np.ndarray:
     """float32 -> bfloat16 bit patterns (round to nearest even), as uint16."""
     b = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)

@@ -14,7 +14,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 ORACLE = os.path.join(ROOT, "oracle")
 PINS = [os.path.join(ROOT, "tests", "test_oracle_points.py"),
         os.path.join(ROOT, "tests", "test_oracle_image_move.py"),
-        os.path.join(ROOT, "tests", "test_oracle_raycast_drift.py")]
+        os.path.join(ROOT, "tests", "test_oracle_raycast_drift.py"),
+        os.path.join(ROOT, "tests", "test_oracle_topk.py")]
 
 # name -> [(exact source text, replacement)], each text occurring once in mem_oracle.c
 MUTANTS = {
@@ -108,6 +109,12 @@ MUTANTS = {
           "        acc_cell[n_accpt] = j;\n        acc_z[n_accpt] = z;\n        ++n_accpt;\n      }\n")],
     "clean-up ray parameter not normalised": [("        float tq = (float)num / (float)den;\n        float ray = fmaf(tq, acc_z[a] - zs, zs);",
                                                "        float tq = (float)num;\n        float ray = fmaf(tq, acc_z[a] - zs, zs);")],
+    # top-k class input (Sec. III-C)
+    "top-k id off by one": [("&& (int)id == k) v += r[2 * j + 1];", "&& (int)id == k + 1) v += r[2 * j + 1];")],
+    "top-k repeated id overwrites": [("&& (int)id == k) v += r[2 * j + 1];", "&& (int)id == k) v = r[2 * j + 1];")],
+    "top-k pair order swapped": [("float id = r[2 * j];", "float id = r[2 * j + 1];"),
+                                 ("&& (int)id == k) v += r[2 * j + 1];", "&& (int)id == k) v += r[2 * j];")],
+    "top-k accepts fractional ids": [("&& id == floorf(id) && (int)id == k)", "&& (int)id == k)")],
     "clean-up ray parameter along x only": [("int32_t num = (qx - sx) * dxs + (qy - sy) * dys;\n        float tq",
                                              "int32_t num = (qx - sx) * dxs;\n        float tq")],
 }
