@@ -135,13 +135,22 @@ typedef struct {
 } mem_map_config;
 
 /* One input source: a row of `channels` values per point (point clouds) or
- * per pixel (images), fused into each listed layer in order. */
+ * per pixel (images), fused into each listed layer in order.
+ * Top-k class input (Sec. III-C: class probabilities may be given as the top
+ * k classes, which saves memory when there are many classes): with topk > 0
+ * a row is instead topk pairs (class id, probability), 2 * topk float32
+ * values (dtype MEM_F32), and `channels` is the class count K of the layers
+ * the source feeds. The row stands for the K-vector holding each listed
+ * probability at its class and zero elsewhere; ids that are not whole numbers
+ * in [0, K) are ignored, a repeated id adds up (float32, in row order). */
+#define MEM_MAX_TOPK 16
 typedef struct {
   const void *data; /* device; [N][channels] or [H][Wi][channels]            */
   int32_t dtype;    /* mem_dtype of the rows                                 */
   int32_t channels;
   int32_t n_layers;
   int32_t layers[MEM_MAX_SOURCE_LAYERS];
+  int32_t topk;     /* 0: dense rows; 1..MEM_MAX_TOPK: rows of topk pairs    */
 } mem_source;
 
 /* Geometric layer ids for mem_get_layer / mem_set_layer (part ignored). */

@@ -576,6 +576,8 @@ static mem_status check_sources(const Map* m, int32_t n_sources, const mem_sourc
     const mem_source& s = sources[q];
     if (!s.data) return fail(MEM_ERR_ARG, "source %d: data is NULL", q);
     if (dtype_size(s.dtype) == 0) return fail(MEM_ERR_ARG, "source %d: bad dtype", q);
+    if (s.topk < 0 || s.topk > MEM_MAX_TOPK) return fail(MEM_ERR_ARG, "source %d: topk in [0, %d]", q, MEM_MAX_TOPK);
+    if (s.topk && s.dtype != MEM_F32) return fail(MEM_ERR_ARG, "source %d: top-k rows are float32 pairs", q);
     if (s.channels < 1 || s.channels > 4096) return fail(MEM_ERR_ARG, "source %d: channels", q);
     if (s.n_layers < 0 || s.n_layers > MEM_MAX_SOURCE_LAYERS) return fail(MEM_ERR_ARG, "source %d: n_layers", q);
     for (int b = 0; b < s.n_layers; ++b) {
@@ -595,7 +597,9 @@ static mem_status check_sources(const Map* m, int32_t n_sources, const mem_sourc
     out[q].dtype = s.dtype;
     out[q].C = s.channels;
     out[q].n_layers = s.n_layers;
-    out[q].vec_ok = ((uintptr_t)s.data & 15) == 0;
+    out[q].topk = s.topk;
+    out[q].unused = 0;
+    out[q].vec_ok = !s.topk && ((uintptr_t)s.data & 15) == 0;
     out[q].has_classmax = 0;
     for (int b = 0; b < s.n_layers; ++b)
       if (m->cfg.layers[s.layers[b]].rule == MEM_RULE_CLASSMAX) out[q].has_classmax = 1;
@@ -656,6 +660,7 @@ void memh::build_fuse_tables(PointJob& job, int acc_raw, const mem_map_config& c
     d.dtype = job.src[q].dtype;
     d.vec = job.src[q].vec_ok;
     d.src = q;
+    d.topk = job.src[q].topk;
   }
   f.n_ck = n;
   for (int k = 0; k < n; ++k) {
@@ -809,8 +814,12 @@ extern "C" mem_status mem_fuse_pointcloud_host(mem_map* mm, int64_t n, const flo
     bytes += (b + 255) & ~(size_t)255;
     return o;
   };
+  // bytes of a source's rows: C values, or 2 * topk float32 for top-k rows
+  auto row_bytes = [&](int q) {
+    return src[q].topk ? (size_t)(2 * src[q].topk) * 4 : (size_t)src[q].C * dtype_size(src[q].dtype);
+  };
   off[0] = take((size_t)n * 12);
-  for (int q = 0; q < n_sources; ++q) off[q + 1] = take((size_t)n * src[q].C * dtype_size(src[q].dtype));
+  for (int q = 0; q < n_sources; ++q) off[q + 1] = take((size_t)n * row_bytes(q));
   if (!m->copy_stream) {
     CK(cudaStreamCreateWithFlags(&m->copy_stream, cudaStreamNonBlocking), "copy stream");
     for (int k = 0; k < 2; ++k) {
@@ -833,11 +842,11 @@ extern "C" mem_status mem_fuse_pointcloud_host(mem_map* mm, int64_t n, const flo
   if (n > 0) {
     CK(cudaMemcpyAsync(d + off[0], xyz, (size_t)n * 12, cudaMemcpyHostToDevice, m->copy_stream), "upload xyz");
     for (int q = 0; q < n_sources; ++q) {
-      CK(cudaMemcpyAsync(d + off[q + 1], sources[q].data, (size_t)n * src[q].C * dtype_size(src[q].dtype),
-                         cudaMemcpyHostToDevice, m->copy_stream),
+      CK(cudaMemcpyAsync(d + off[q + 1], sources[q].data, (size_t)n * row_bytes(q), cudaMemcpyHostToDevice,
+                         m->copy_stream),
          "upload source");
       src[q].data = d + off[q + 1];
-      src[q].vec_ok = 1;  // 256-byte aligned
+      src[q].vec_ok = !src[q].topk;  // 256-byte aligned
     }
   }
   // the job block follows the inputs on the copy stream; the kernels wait for both

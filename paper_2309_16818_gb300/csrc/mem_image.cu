@@ -70,7 +70,6 @@ __device__ __forceinline__ void fuse_pixel_warp(const MapDev& md, const ImgParam
   const int lane = (threadIdx.x + threadIdx.y * blockDim.x) & 31;
   for (int q = 0; q < ip.n_src; ++q) {
     const SrcDev& s = ip.src[q];
-    const int64_t row = p * s.C;
     for (int b = 0; b < s.n_layers; ++b) {
       const int l = s.layers[b];
       const LayerDev& L = md.L[l];
@@ -79,7 +78,7 @@ __device__ __forceinline__ void fuse_pixel_warp(const MapDev& md, const ImgParam
         float best = -INFINITY;
         int bid = 0x7fffffff;
         for (int c = lane; c < s.C; c += 32) {
-          const float v = ld_any(s.data, s.dtype, row + c);
+          const float v = src_val(s, p, c);
           if (v > best) {
             best = v;
             bid = c;
@@ -102,7 +101,7 @@ __device__ __forceinline__ void fuse_pixel_warp(const MapDev& md, const ImgParam
       } else {
         const float s02 = (L.rule == MEM_RULE_GAUSS && obs) ? L.gvar[g] : 0.f;
         const RuleCoef co = rule_coef(L, 1.f, 1.f, obs, s02);
-        for (int c = lane; c < s.C; c += 32) apply_rule(L, g * L.S + c, ld_any(s.data, s.dtype, row + c), co);
+        for (int c = lane; c < s.C; c += 32) apply_rule(L, g * L.S + c, src_val(s, p, c), co);
         if (L.rule == MEM_RULE_GAUSS) {
           __syncwarp();
           if (lane == 0) L.gvar[g] = co.var_new;

@@ -99,6 +99,8 @@ struct SrcDev {
   int vec_ok;        // data is 16-byte aligned: rows may be read with vector loads
   int has_classmax;  // a CLASSMAX layer is bound: track the arg-max
   int acc_off;       // offset of this source's sums (then maxima) in a partial record
+  int topk;          // > 0: rows are topk (class id, probability) float32 pairs over C classes
+  int unused;
 };
 
 constexpr int kFuseQ = 32;  // stage columns of the fuse kernel per round
@@ -112,7 +114,8 @@ struct __align__(16) ChunkDesc {
   int dtype, vec;   // storage, 16-byte aligned rows
   int am;           // arg-max value column of the source (-1: none); bit 30: last chunk
   int src;
-  int unused[2];
+  int topk;         // > 0: the source's rows are topk (class id, probability) pairs
+  int unused;
 };
 
 // Stage layout of the fuse kernel, built on the host for a call whose
@@ -210,6 +213,24 @@ __device__ __forceinline__ float ld_any(const void* base, int dtype, int64_t off
     case MEM_F16: return __half2float(((const __half*)base)[off]);
     default: return (float)__ldg((const unsigned char*)base + off);
   }
+}
+
+// Class c of a row of top-k (class id, probability) pairs over C classes: the
+// sum, in row order, of the probabilities listed for c (ids that are not whole
+// numbers in [0, C) are ignored).
+__device__ __forceinline__ float topk_val(const float* __restrict__ r, int k, int C, int c) {
+  float v = 0.f;
+  for (int j = 0; j < k; ++j) {
+    const float id = __ldg(r + 2 * j);
+    if (id >= 0.f && id < (float)C && id == floorf(id) && (int)id == c) v = __fadd_rn(v, __ldg(r + 2 * j + 1));
+  }
+  return v;
+}
+
+// channel c of row `row` of a source (dense or top-k rows)
+__device__ __forceinline__ float src_val(const SrcDev& s, int64_t row, int c) {
+  if (s.topk) return topk_val((const float*)s.data + row * 2 * s.topk, s.topk, s.C, c);
+  return ld_any(s.data, s.dtype, row * s.C + c);
 }
 
 // Four consecutive channels c0..c0+3 of row `row` (channels >= C read as 0).

@@ -593,6 +593,7 @@ __device__ __forceinline__ void build_columns(SumSmem& s, int n_src, int r0, int
         d.dtype = s.src[q].dtype;
         d.vec = s.src[q].vec_ok;
         d.src = q;
+        d.topk = s.src[q].topk;
       }
     }
     s.n_ck = n;
@@ -629,6 +630,21 @@ __device__ __forceinline__ void build_columns(SumSmem& s, int n_src, int r0, int
 
 // four consecutive channels of a row (fewer at the end of the row)
 __device__ __forceinline__ void ld_chunk(const ChunkDesc& d, int64_t row, float v[4]) {
+  if (d.topk) {  // expand the row's (class id, probability) pairs into the chunk's channels
+    const float* __restrict__ r = (const float*)d.data + row * 2 * d.topk;
+#pragma unroll
+    for (int w = 0; w < 4; ++w) v[w] = 0.f;
+    for (int j = 0; j < d.topk; ++j) {
+      const float id = __ldg(r + 2 * j);
+      if (id >= 0.f && id < (float)d.C && id == floorf(id)) {
+        const int c = (int)id - d.ch0;
+#pragma unroll
+        for (int w = 0; w < 4; ++w)
+          if (c == w && w < d.n) v[w] = __fadd_rn(v[w], __ldg(r + 2 * j + 1));
+      }
+    }
+    return;
+  }
   const int64_t off = row * d.C + d.ch0;
   if (d.n == 4 && d.vec && (off & 3) == 0) {
     if (d.dtype == MEM_F32) {
@@ -1052,7 +1068,7 @@ __global__ void __launch_bounds__(kFT, 6) k_fuse_tiles(MapDev md, const PointJob
           float pb = -INFINITY;
           int pi = 0x7fffffff;
           for (int k = 0; k < src.C; ++k) {
-            const float v = ld_any(src.data, src.dtype, (int64_t)s.idx[t] * src.C + k);
+            const float v = src_val(src, (int64_t)s.idx[t], k);
             if (v > pb) {
               pb = v;
               pi = k;

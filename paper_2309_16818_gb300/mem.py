@@ -54,7 +54,15 @@ class MapConfig(C.Structure):
 
 class Source(C.Structure):
     _fields_ = [("data", C.c_void_p), ("dtype", C.c_int32), ("channels", C.c_int32),
-                ("n_layers", C.c_int32), ("layers", C.c_int32 * MAX_SOURCE_LAYERS)]
+                ("n_layers", C.c_int32), ("layers", C.c_int32 * MAX_SOURCE_LAYERS), ("topk", C.c_int32)]
+
+
+@dataclass
+class TopK:
+    """Top-k class input (mem_source.topk): ``pairs`` a float32 tensor [N, 2k] (or [H, Wi, 2k])
+    of (class id, probability), ``K`` the class count of the layers it feeds."""
+    pairs: object
+    K: int
 
 
 class MemError(RuntimeError):
@@ -253,11 +261,15 @@ class Map:
     def _sources(self, sources, keep, on_host=False):
         arr = (Source * MAX_SOURCES)()
         for i, (t, layers) in enumerate(sources):
+            K = None
+            if isinstance(t, TopK):
+                t, K = t.pairs, t.K
             assert t.is_cuda != on_host and t.is_contiguous()
             keep.append(t)
             arr[i].data = t.data_ptr()
             arr[i].dtype = _dtype_code(t)
-            arr[i].channels = t.shape[-1]
+            arr[i].channels = t.shape[-1] if K is None else K
+            arr[i].topk = 0 if K is None else t.shape[-1] // 2
             arr[i].n_layers = len(layers)
             for k, l in enumerate(layers):
                 arr[i].layers[k] = l
