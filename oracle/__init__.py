@@ -108,6 +108,7 @@ def lib():
         L.orc_harmonic_fill.argtypes = [C.c_int32, C.c_int32, P, P, C.c_double, C.c_int32, P]
         L.orc_harmonic_fill.restype = C.c_int32
         L.orc_last_fuse_info.argtypes = [P, P, P]
+        L.orc_normals.argtypes = [P, P, P, P]
         _lib = L
     return _lib
 
@@ -280,6 +281,20 @@ class OracleMap:
         nv = lib().orc_fuse_image(C.byref(self.cfg), C.byref(self.st), H, Wi, len(sources),
                                   C.cast(src, C.c_void_p), _p(Kd), _p(T), _p(vis), _p(pix))
         return dict(n_visible=nv, vis=vis, pix=pix)
+
+    def normals(self):
+        """Surface normals of the elevation layer: (normals float32 [W*W, 3], ok uint8 [W*W])."""
+        W2 = self.p.W * self.p.W
+        out = np.zeros((W2, 3), np.float32)
+        ok = np.zeros(W2, np.uint8)
+        lib().orc_normals(C.byref(self.cfg), C.byref(self.st), _p(out), _p(ok))
+        return out, ok
+
+    def pca(self, l: int, n_comp: int = 3):
+        """PCA of a feature layer over its observed cells (see pca_of_features)."""
+        from .plugins import pca_of_features
+        obs = self.obs[l].astype(bool)
+        return pca_of_features(self.layer_values(l), obs, n_comp)
 
     def move(self, robot_xy):
         xy = np.ascontiguousarray(robot_xy, dtype=np.float64)

@@ -642,3 +642,50 @@ int32_t orc_harmonic_fill(int32_t H, int32_t W, double *h, const uint8_t *known,
   if (residual) *residual = r;
   return it;
 }
+
+/* ------------------------------------------------------------------------ */
+/* surface normals of the elevation layer                                   */
+
+/* Slope along one axis at a cell from its two neighbours (a = lower index,
+ * b = higher index) in binary32: central difference over 2 res when both are
+ * valid, one-sided over res with the cell itself when one is. Returns 0 when
+ * neither neighbour is valid. */
+static int axis_slope(float hm, int va, float ha, int vb, float hb, float res, float *g) {
+  if (va && vb) {
+    *g = (hb - ha) / (2.0f * res);
+    return 1;
+  }
+  if (vb) {
+    *g = (hb - hm) / res;
+    return 1;
+  }
+  if (va) {
+    *g = (hm - ha) / res;
+    return 1;
+  }
+  return 0;
+}
+
+void orc_normals(const orc_cfg *c, const orc_state *s, float *out, uint8_t *ok) {
+  int W = c->W;
+  float res = (float)c->res;
+  for (int32_t iy = 0; iy < W; ++iy)
+    for (int32_t ix = 0; ix < W; ++ix) {
+      int64_t j = (int64_t)iy * W + ix;
+      out[3 * j] = out[3 * j + 1] = out[3 * j + 2] = 0.0f;
+      ok[j] = 0;
+      if (!s->valid[j]) continue;
+      float hm = (float)s->h[j];
+      int vl = ix > 0 && s->valid[j - 1], vr = ix + 1 < W && s->valid[j + 1];
+      int vd = iy > 0 && s->valid[j - W], vu = iy + 1 < W && s->valid[j + W];
+      float gx, gy;
+      if (!axis_slope(hm, vl, vl ? (float)s->h[j - 1] : 0.0f, vr, vr ? (float)s->h[j + 1] : 0.0f, res, &gx)) continue;
+      if (!axis_slope(hm, vd, vd ? (float)s->h[j - W] : 0.0f, vu, vu ? (float)s->h[j + W] : 0.0f, res, &gy)) continue;
+      float n2 = fmaf(gx, gx, fmaf(gy, gy, 1.0f));
+      float inv = 1.0f / sqrtf(n2);
+      out[3 * j] = -gx * inv;
+      out[3 * j + 1] = -gy * inv;
+      out[3 * j + 2] = inv;
+      ok[j] = 1;
+    }
+}

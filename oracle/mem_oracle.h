@@ -104,6 +104,11 @@ int32_t orc_bresenham(int32_t sx, int32_t sy, int32_t ex, int32_t ey, int32_t *x
 int64_t orc_fuse_image(const orc_cfg *c, orc_state *s, int32_t H, int32_t Wi, int32_t n_src,
                        const orc_src *src, const double K[4], const double T[16], uint8_t *vis,
                        int32_t *pix);
+/* Surface normals of the elevation layer (Table I "normal calculation"; the reading is in
+   the design notes): out[j] = (-gx, -gy, 1) / |(-gx, -gy, 1)|, with slopes from central
+   differences of the valid logical neighbours (one-sided where one is missing);
+   ok[j] = 0 where the cell is invalid or has no valid neighbour along x or along y. */
+void orc_normals(const orc_cfg *c, const orc_state *s, float *out, uint8_t *ok);
 int32_t orc_harmonic_fill(int32_t H, int32_t W, double *h, const uint8_t *known, double tol,
                           int32_t max_sweeps, double *residual);
 

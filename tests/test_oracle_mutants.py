@@ -15,7 +15,8 @@ ORACLE = os.path.join(ROOT, "oracle")
 PINS = [os.path.join(ROOT, "tests", "test_oracle_points.py"),
         os.path.join(ROOT, "tests", "test_oracle_image_move.py"),
         os.path.join(ROOT, "tests", "test_oracle_raycast_drift.py"),
-        os.path.join(ROOT, "tests", "test_oracle_topk.py")]
+        os.path.join(ROOT, "tests", "test_oracle_topk.py"),
+        os.path.join(ROOT, "tests", "test_oracle_plugins.py")]
 
 # name -> [(exact source text, replacement)], each text occurring once in mem_oracle.c
 MUTANTS = {
@@ -109,6 +110,13 @@ MUTANTS = {
           "        acc_cell[n_accpt] = j;\n        acc_z[n_accpt] = z;\n        ++n_accpt;\n      }\n")],
     "clean-up ray parameter not normalised": [("        float tq = (float)num / (float)den;\n        float ray = fmaf(tq, acc_z[a] - zs, zs);",
                                                "        float tq = (float)num;\n        float ray = fmaf(tq, acc_z[a] - zs, zs);")],
+    # surface normals (Table I "normal calculation")
+    "normal central difference over one cell": [("*g = (hb - ha) / (2.0f * res);", "*g = (hb - ha) / res;")],
+    "normal one-sided differences swapped": [("*g = (hb - hm) / res;", "*g = (hm - ha) / res;")],
+    "normal not normalised": [("float inv = 1.0f / sqrtf(n2);", "float inv = 1.0f;")],
+    "normal slope sign flipped": [("out[3 * j] = -gx * inv;", "out[3 * j] = gx * inv;")],
+    "normal ignores invalid neighbours":
+        [("int vl = ix > 0 && s->valid[j - 1], vr = ix + 1 < W && s->valid[j + 1];", "int vl = ix > 0, vr = ix + 1 < W;")],
     # top-k class input (Sec. III-C)
     "top-k id off by one": [("&& (int)id == k) v += r[2 * j + 1];", "&& (int)id == k + 1) v += r[2 * j + 1];")],
     "top-k repeated id overwrites": [("&& (int)id == k) v += r[2 * j + 1];", "&& (int)id == k) v = r[2 * j + 1];")],
@@ -216,4 +224,48 @@ def test_unaltered_unet_oracle_passes_the_pins():
 @pytest.mark.parametrize("name", sorted(UNET_MUTANTS))
 def test_planted_unet_mistake_fails_a_pin(name):
     rc, out = _unet_pins(*UNET_MUTANTS[name])
+    assert rc == 1, f"{name}: the pins did not fail (exit {rc})\n{out}"
+
+
+# the PCA plugin oracle (oracle/plugins.py): name -> (exact source text, replacement)
+PCA_MUTANTS = {
+    "features not centred": ("    Xc = X - m\n", "    Xc = X\n"),
+    "smallest eigenvalues taken": ("order = np.argsort(-w, kind=\"stable\")[:n_comp]", "order = np.argsort(w, kind=\"stable\")[:n_comp]"),
+    "covariance normalised by n - 1": ("S = Xc.T @ Xc / n", "S = Xc.T @ Xc / (n - 1)"),
+    "sign from the smallest component": ("i = int(np.argmax(np.abs(V[k])))", "i = int(np.argmin(np.abs(V[k])))"),
+    "unobserved cells included": ("    X = f[obs]\n", "    X = f\n"),
+}
+
+_RUN_PCA = r'''
+import sys, types
+sys.path.insert(0, ROOT)
+import oracle
+src = open(ROOT + "/oracle/plugins.py").read()
+if OLD:
+    assert src.count(OLD) == 1, OLD
+    src = src.replace(OLD, NEW)
+m = types.ModuleType("oracle.plugins")
+m.__file__ = ROOT + "/oracle/plugins.py"
+exec(compile(src, m.__file__, "exec"), m.__dict__)
+sys.modules["oracle.plugins"] = m
+oracle.plugins = m
+import pytest
+sys.exit(pytest.main(["-x", "-q", "-p", "no:cacheprovider", ROOT + "/tests/test_oracle_plugins.py"]))
+'''
+
+
+def _pca_pins(old, new):
+    code = f"ROOT = {ROOT!r}\nOLD = {old!r}\nNEW = {new!r}\n" + _RUN_PCA
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True)
+    return r.returncode, r.stdout[-2000:] + r.stderr[-2000:]
+
+
+def test_unaltered_pca_oracle_passes_the_pins():
+    rc, out = _pca_pins("", "")
+    assert rc == 0, out
+
+
+@pytest.mark.parametrize("name", sorted(PCA_MUTANTS))
+def test_planted_pca_mistake_fails_a_pin(name):
+    rc, out = _pca_pins(*PCA_MUTANTS[name])
     assert rc == 1, f"{name}: the pins did not fail (exit {rc})\n{out}"
