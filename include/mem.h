@@ -309,6 +309,38 @@ mem_status mem_get_stats(mem_map *m, void *stream, int64_t out[4]);
  * ray cast"; see mem_map_config. MEM_ERR_ARG for a bad index. */
 mem_status mem_get_drift(mem_map *m, int32_t map_index, void *stream, double out[3]);
 
+/* Post-processing plugins (Sec. III-D: plugins read the map layers already on
+ * the GPU and produce new layers).
+ *
+ * Surface normals of the elevation layer of map `map_index` (Table I "normal
+ * calculation"; the reading is this library's): per valid cell the slopes gx,
+ * gy from central differences of its valid logical neighbours over 2 res, or
+ * one-sided differences with the cell itself over res where one neighbour is
+ * invalid or outside the map; normal = (-gx, -gy, 1) / |(-gx, -gy, 1)|.
+ *   normals  device float32 [W*W][3] (out; 0 where there is no normal)
+ *   ok       device uint8 [W*W] (out, optional): 1 where the cell is valid and
+ *            has a valid neighbour along x and along y
+ * Logical cell order (iy * W + ix). Asynchronous on `stream`. */
+mem_status mem_compute_normals(mem_map *m, int32_t map_index, float *normals, uint8_t *ok, void *stream);
+
+/* PCA layer of a feature layer (the plugin of Sec. III-D's figure that turns
+ * feature layers into a PCA layer; the reading is this library's): over the
+ * cells of map `map_index` where `layer` is observed, the mean m and the
+ * covariance (1/n) sum (f - m)(f - m)^T of its values, the n_comp
+ * eigenvectors of largest eigenvalue (each signed so that its
+ * largest-magnitude component is positive), and every observed cell's
+ * projections (f - m) . v_k (0 elsewhere).
+ *   layer    any multi-modal layer but CLASSMAX, 1..128 channels
+ *   n_comp   1..min(8, channels)
+ *   proj     device float32 [W*W][n_comp] (out, logical cell order)
+ *   info     device float32 (out, optional): n_comp eigenvalues, then the
+ *            n_comp vectors [n_comp][channels], then the mean [channels]
+ * Float32 sums per block added in float64; eigenvectors by Jacobi sweeps in
+ * float32. The map owns a scratch buffer for it (allocated on the first call,
+ * which synchronises the stream). MEM_ERR_ARG for bad indices or sizes. */
+mem_status mem_pca_layer(mem_map *m, int32_t map_index, int32_t layer, int32_t n_comp, float *proj, float *info,
+                         void *stream);
+
 /* Diffusion (harmonic) inpainting of a batch of map crops, the fallback of the
  * learned inpainting and the reference it is judged against: each unknown
  * cell (known == 0) becomes the mean of its in-crop 4-neighbours (zero-flux

@@ -11,7 +11,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmem.so")
-SOURCES = ["mem_api.cu", "mem_points.cu", "mem_image.cu", "mem_noalloc.cu", "mem_inpaint.cu", "mem_unet.cu"]
+SOURCES = ["mem_api.cu", "mem_points.cu", "mem_image.cu", "mem_noalloc.cu", "mem_inpaint.cu", "mem_unet.cu",
+           "mem_plugins.cu"]
 HEADERS = ["mem_internal.cuh", "mem_host.h"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 

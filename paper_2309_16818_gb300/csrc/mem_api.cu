@@ -61,6 +61,7 @@ mem_status api_fail(mem_status s, const char* fmt, ...) {
   return s;
 }
 mem_status api_cuda_fail(cudaError_t e, const char* what) { return cuda_fail(e, what); }
+Map* map_of(mem_map* mm) { return &mm->m; }
 }  // namespace memh
 
 // ---------------------------------------------------------------------------
@@ -513,6 +514,7 @@ extern "C" mem_status mem_destroy_map(mem_map* mm) {
     if (m->stage_done[k]) cudaEventDestroy(m->stage_done[k]);
   }
   if (m->copy_stream) cudaStreamDestroy(m->copy_stream);
+  if (m->pca_buf) cudaFree(m->pca_buf);
   delete mm;
   return MEM_OK;
 }

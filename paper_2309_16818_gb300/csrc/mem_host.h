@@ -54,6 +54,9 @@ struct Map {
   cudaEvent_t stage_copied[2] = {}, stage_done[2] = {};
   cudaStream_t copy_stream = nullptr;
   int stage_slot = 0;
+  // scratch of the PCA plugin (grown on demand)
+  void* pca_buf = nullptr;
+  size_t pca_cap = 0;
   // allocations to free
   std::vector<void*> allocs;
   std::vector<void*> scratch_allocs;
@@ -95,6 +98,7 @@ cudaError_t launch_time_update(Map* m, cudaStream_t st);
 // the raw slot length `acc_raw` set), as the fuse kernel reads them
 void build_fuse_tables(memk::PointJob& job, int acc_raw, const mem_map_config& cfg);
 mem_status api_fail(mem_status s, const char* fmt, ...);
+Map* map_of(mem_map* mm);
 mem_status api_cuda_fail(cudaError_t e, const char* what);
 
 }  // namespace memh

@@ -31,7 +31,8 @@ EXPORTS = ["mem_create_map", "mem_destroy_map", "mem_move_map", "mem_fuse_pointc
            "mem_autotune_batch", "mem_inpaint_diffusion", "mem_unet_create", "mem_unet_destroy",
            "mem_unet_param_count", "mem_unet_set_params", "mem_unet_get_params", "mem_unet_forward",
            "mem_unet_gradients", "mem_unet_train_step", "mem_unet_check", "mem_inject_fault",
-           "mem_noalloc_check", "mem_get_drift", "mem_unet_prepare"]
+           "mem_noalloc_check", "mem_get_drift", "mem_unet_prepare", "mem_compute_normals",
+           "mem_pca_layer"]
 NOALLOC_MAX_POINTS = 1 << 18
 PROFILE_SLOTS = ["key", "digit_scan", "radix_sort", "unused3", "fuse_tiles", "fuse_cross",
                  "time_var", "image", "move", "drift", "raycast"]
@@ -105,6 +106,7 @@ def lib():
             "mem_unet_check": [P, P], "mem_inject_fault": [P, I32],
             "mem_noalloc_check": [P], "mem_get_drift": [P, I32, P, P],
             "mem_unet_prepare": [I32, I32, I32, P, P, P, P, P, P, P],
+            "mem_compute_normals": [P, I32, P, P, P], "mem_pca_layer": [P, I32, I32, I32, P, P, P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -395,6 +397,26 @@ class Map:
         calls = np.zeros(16, np.int64)
         _ck(lib().mem_get_profile(self._h, ms.ctypes.data, calls.ctypes.data))
         return {k: (float(ms[i]), int(calls[i])) for i, k in enumerate(PROFILE_SLOTS)}
+
+    def normals(self, map_index=0, stream=None):
+        """Surface normals of the elevation layer: (float32 [W*W, 3], uint8 ok [W*W]) cuda."""
+        torch = _torch()
+        out = torch.empty((self.W * self.W, 3), dtype=torch.float32, device="cuda")
+        ok = torch.empty(self.W * self.W, dtype=torch.uint8, device="cuda")
+        _ck(lib().mem_compute_normals(self._h, map_index, C.c_void_p(out.data_ptr()), C.c_void_p(ok.data_ptr()),
+                                      _stream(stream)))
+        return out, ok
+
+    def pca(self, layer, n_comp=3, map_index=0, stream=None):
+        """PCA layer of a feature layer: (projections float32 [W*W, n_comp], eigenvalues
+        [n_comp], vectors [n_comp, C], mean [C]) cuda."""
+        torch = _torch()
+        Cc = self.layers[layer].channels
+        proj = torch.empty((self.W * self.W, n_comp), dtype=torch.float32, device="cuda")
+        info = torch.empty(n_comp + n_comp * Cc + Cc, dtype=torch.float32, device="cuda")
+        _ck(lib().mem_pca_layer(self._h, map_index, layer, n_comp, C.c_void_p(proj.data_ptr()),
+                                C.c_void_p(info.data_ptr()), _stream(stream)))
+        return proj, info[:n_comp], info[n_comp:n_comp + n_comp * Cc].view(n_comp, Cc), info[n_comp + n_comp * Cc:]
 
     def get_drift(self, map_index=0, stream=None):
         """{drift: shift applied by the last point fuse, drift_points: points in its mean,
