@@ -251,6 +251,24 @@ def run_ours(args):
         wall = time.perf_counter() - t0
     m.check()
     step_ms = [a.elapsed_time(b) for a, b in evs]
+
+    # step-time statistics over 60 further steps each: cold (L2 flushed before every step) and
+    # warm (no flush; a pose's cloud may still be in L2 from ten steps earlier)
+    def step_stats(flushed):
+        ev = []
+        for i in range(60):
+            if flushed:
+                flush(i)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step(i % n_pose)
+            b.record(stream)
+            ev.append((a, b))
+        torch.cuda.synchronize()
+        t = np.array([a.elapsed_time(b) for a, b in ev])
+        return {"median_ms": round(float(np.median(t)), 4), "p10_ms": round(float(np.percentile(t, 10)), 4),
+                "p90_ms": round(float(np.percentile(t, 90)), 4), "steps": len(t)}
+    stats_cold, stats_warm = step_stats(True), step_stats(False)
     # per-kernel times: a separate pass with an event pair around every launch
     # (eager launches, so a little slower than the graph-replayed timed steps)
     m.set_profiling(True)
@@ -347,6 +365,12 @@ def run_ours(args):
                        "page-locked host memory each step; whole-run throughput, no L2 flush inside"}
 
     extra = {}
+    if not args.no_small:
+        extra["config1"] = bench_config1(args, dev, ws)
+    if not args.no_topk:
+        extra["topk"] = bench_topk(args, dev, flush, ws, c, xyz, rgb)
+    if not args.no_plugins:
+        extra["plugins"] = bench_plugins(args, dev, flush, ws, c, xyz)
     if not args.no_raycast:
         srcs = [[(rgb[k], [0]), (prb[k], [1, 2, 3])] for k in range(n_pose)]
         extra["raycast_drift"] = bench_raycast_drift(args, dev, flush, ws, c, xyz, srcs)
@@ -374,6 +398,7 @@ def run_ours(args):
                        "radix_passes": P, "l2": "512 MiB write between timed steps, outside the per-step events",
                        "parallelism": f"replicas x{ws} (one independent map per GPU)"},
             "map_updates_per_s": round(ws * K / dev_s_max, 2),
+            "step_ms": {"cold_l2_flushed": stats_cold, "warm": stats_warm},
             "hbm_frac_step": round(step_frac, 4),
             "roofline": roofline, "kernels": kern, "gpu_launches": gpu_launches,
             "wall_s": round(wall, 3), "clocks": clk.summary(), "e2e": e2e,
@@ -400,6 +425,109 @@ def _timed_steps(step, n_pose, K, warmup, flush, stream):
         evs.append((a, b))
     torch.cuda.synchronize()
     return float(np.mean([a.elapsed_time(b) for a, b in evs]))
+
+
+def bench_config1(args, dev, ws):
+    """The small plain workload: one 20k-point cloud (xyz + RGB) into a 200 x 200 map at
+    0.04 m with height and colour-average layers; launch-latency bound, so reported as the
+    median microseconds per call over 200 calls (warm, graph-replayed on a stream of its own)."""
+    import torch
+    from paper_2309_16818_gb300 import mem as M
+    from paper_2309_16818_gb300 import synth
+    c = synth.config1()
+    cl = c["cloud"]
+    m = M.Map(c["W"], c["res"], [M.Layer(3, M.LATEST)], max_points=cl.n + 1024)
+    x = torch.from_numpy(cl.xyz).to(dev)
+    r = torch.from_numpy(cl.rgb).to(dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(10):
+        m.fuse_pointcloud(x, cl.T, [(r, [0])])
+    ev = []
+    for _ in range(200):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        m.fuse_pointcloud(x, cl.T, [(r, [0])])
+        b.record(stream)
+        ev.append((a, b))
+    torch.cuda.synchronize()
+    m.check()
+    t = float(np.median([a.elapsed_time(b) for a, b in ev]))
+    m.close()
+    return {"workload": "20,000-point cloud (xyz + RGB), 200x200 map at 0.04 m, height + colour average",
+            "us_per_call_median": round(1e3 * t, 2), "points_per_s": round(ws * cl.n / (t / 1e3), 1),
+            "map_updates_per_s": round(ws * 1e3 / t, 1)}
+
+
+def bench_topk(args, dev, flush, ws, c, xyz, rgb):
+    """The headline workload with each point's 20 class probabilities given as its top 3
+    (class id, probability) pairs (24 B instead of 80 B per point)."""
+    import torch
+    from paper_2309_16818_gb300 import mem as M
+    from paper_2309_16818_gb300 import synth
+    n_pose = len(c["scans"])
+    pairs = [torch.from_numpy(synth.topk_pairs(s.probs, 3)).to(dev) for s in c["scans"]]
+    m = M.Map(c["W"], c["res"], multimodal_layer_specs(M), max_points=max(s.n for s in c["scans"]) + 1024)
+    stream = torch.cuda.current_stream()
+
+    def step(k):
+        m.move(c["poses"][k][:2])
+        m.fuse_pointcloud(xyz[k], c["scans"][k].T, [(rgb[k], [0]), (M.TopK(pairs[k], 20), [1, 2, 3])])
+
+    ms = _timed_steps(step, n_pose, max(10, args.steps), args.warmup, flush, stream)
+    m.check()
+    m.close()
+    npts = float(np.mean([s.n for s in c["scans"]]))
+    t = max_over_ranks(ms / 1e3, ws)
+    return {"workload": "headline poses, class probabilities as top-3 (class id, probability) pairs",
+            "ms_per_step": round(1e3 * t, 4), "points_per_s": round(ws * npts / t, 1),
+            "class_bytes_per_point": 24, "dense_class_bytes_per_point": 80}
+
+
+def bench_plugins(args, dev, flush, ws, c, xyz):
+    """Post-processing plugins on the headline map after one pose: surface normals of the
+    500 x 500 elevation layer, and the PCA layer (3 components) of a 64-d feature layer filled
+    by one 848 x 480 camera."""
+    import torch
+    from paper_2309_16818_gb300 import mem as M
+    from paper_2309_16818_gb300 import synth
+    stream = torch.cuda.current_stream()
+    m = M.Map(c["W"], c["res"], [M.Layer(64, M.GAUSS, var_meas=1.0)])
+    m.move(c["poses"][0][:2])
+    m.fuse_pointcloud(xyz[0], c["scans"][0].T)
+    cam = synth.cameras_around(3, c["poses"][0], c["terrain"])[0]
+    m.fuse_image(cam.H, cam.Wi, cam.K, cam.T, [(torch.from_numpy(cam.feat).to(dev), [0])])
+    W2 = c["W"] ** 2
+    nrm = torch.empty((W2, 3), dtype=torch.float32, device=dev)
+    ok = torch.empty(W2, dtype=torch.uint8, device=dev)
+
+    def timed(fn, reps=20):
+        for _ in range(3):
+            fn()
+        ev = []
+        for i in range(reps):
+            flush(i)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            ev.append((a, b))
+        torch.cuda.synchronize()
+        return float(np.median([a.elapsed_time(b) for a, b in ev]))
+
+    t_n = timed(lambda: M.lib().mem_compute_normals(m._h, 0, M.C.c_void_p(nrm.data_ptr()),
+                                                    M.C.c_void_p(ok.data_ptr()), M._stream(None)))
+    m.pca(0, 3)
+    t_p = timed(lambda: m.pca(0, 3))
+    obs = int(m.get_layer(0, part=M.PART_OBSERVED).sum().item())
+    m.check()
+    m.close()
+    peak, _ = peaks()
+    nbytes = W2 * (4 + 4 + 12 + 1)  # h and flags read, normal and mask written (neighbours from cache)
+    return {"normals": {"workload": "500x500 elevation layer", "us_per_call": round(1e3 * t_n, 2),
+                        "achieved_gbs": round(nbytes / (t_n / 1e3) / 1e9, 1),
+                        "hbm_frac": round(nbytes / (t_n / 1e3) / 1e9 / peak, 4)},
+            "pca": {"workload": f"64-d feature layer of a 500x500 map, {obs} observed cells, 3 components",
+                    "ms_per_call": round(t_p, 4)}}
 
 
 def bench_raycast_drift(args, dev, flush, ws, c, xyz, srcs):
@@ -559,6 +687,7 @@ def bench_batched(args, dev, flush, ws):
     cb = cell_bytes(layers, M)
     cells = st["cells"]
     algo = n * 12 + st["kept"] * (3 + 32) + cells * cb
+    cpu = batched_cpu_baseline(B) if (not args.no_cpu and int(os.environ.get("RANK", "0")) == 0) else None
     return {"workload": f"{B} maps 200x200 @ 0.05 m, {n} points (log-uniform 5k-60k per map), RGB avg + 16-d BF16 Gaussian features",
             "batched_map_updates_per_s": round(ws * B / t_batch, 1),
             "plain_map_updates_per_s": round(ws * B / t_plain, 1),
@@ -566,7 +695,42 @@ def bench_batched(args, dev, flush, ws):
             "speedup": round(t_plain / t_batch, 3), "ms_batched": round(1e3 * t_batch, 4),
             "ms_plain_512_calls": round(1e3 * t_plain, 4), "hbm_frac": round(algo / t_batch / 1e9 / peak, 4),
             "kernels_ms": prof_b, "autotuned": tuning,
-            "autotune_candidates_ms": [round(x, 4) for x in cand_ms]}
+            "autotune_candidates_ms": [round(x, 4) for x in cand_ms], "cpu_baseline": cpu}
+
+
+def _oracle_maps_worker(indices):
+    """CPU oracle over the batched workload's maps `indices` (run in a worker process): the
+    seconds spent in the oracle's fuse calls and the points fused."""
+    import oracle as O
+    from paper_2309_16818_gb300 import synth
+    clouds = [synth.config4_cloud(b) for b in indices]
+    layers = [O.Layer(3, O.LATEST), O.Layer(16, O.GAUSS, store=O.BF16)]
+    t, pts = 0.0, 0
+    for cl in clouds:
+        o = O.OracleMap(O.Params(W=200, res=0.05, layers=layers))
+        t0 = time.perf_counter()
+        o.fuse_points(cl.xyz, cl.T, [(cl.rgb, [0]), ((cl.feat,), [1])])
+        t += time.perf_counter() - t0
+        pts += cl.n
+    return t, pts
+
+
+def batched_cpu_baseline(B):
+    """The oracle over all B maps of the batched workload on every allowed host core (one
+    process per core, maps dealt round-robin; the time is the slowest process's fuse time), and
+    single-threaded on the first 32 maps."""
+    import multiprocessing as mp
+    cores = len(os.sched_getaffinity(0))
+    parts = [list(range(k, B, cores)) for k in range(cores)]
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.map(_oracle_maps_worker, parts)
+    t_par = max(r[0] for r in res)
+    pts = sum(r[1] for r in res)
+    t1, p1 = _oracle_maps_worker(list(range(32)))
+    return {"all_cores": {"map_updates_per_s": round(B / t_par, 1), "points_per_s": round(pts / t_par, 1),
+                          "cores": cores, "kind": "oracle", "sample": f"all {B} maps, one process per core"},
+            "single_thread": {"map_updates_per_s": round(32 / t1, 1), "points_per_s": round(p1 / t1, 1),
+                              "cores": 1, "kind": "oracle", "sample": "the first 32 maps"}}
 
 
 def bench_inpaint(args, dev, flush, ws):
@@ -603,6 +767,13 @@ def bench_inpaint(args, dev, flush, ws):
     pred = torch.empty_like(fill)
     net.forward(x3, fill, out=pred)  # warm-up (allocates activations)
     t_inf, _ = ev(lambda: net.forward(x3, fill, out=pred))
+
+    def learned():  # the whole learned path: diffusion fill, input preparation, network
+        xx, ff, _, _ = I.prepare(h, k, tol=1e-6)
+        return net.forward(xx, ff, out=pred)
+
+    learned()
+    t_e2e, _ = ev(learned)
     c1, c2, c3, c4 = widths
     macs = 0
     for lvl, convs in enumerate([[(3, c1), (c1, c1), (c2 + c1, c1), (c1, c1)],
@@ -627,6 +798,8 @@ def bench_inpaint(args, dev, flush, ws):
     return {"workload": f"{B} crops of {S}x{S} cells (height fill, hidden mask, log variance), U-Net widths {widths}",
             "diffusion_ms": round(1e3 * t_fill, 3), "diffusion_max_sweeps": int(its.max().item()),
             "unet_inference_ms": round(1e3 * t_inf, 3), "unet_inference_crops_per_s": round(ws * B / t_inf, 1),
+            "learned_inpainting_end_to_end_ms": round(1e3 * t_e2e, 3),
+            "learned_inpainting_crops_per_s": round(ws * B / t_e2e, 1),
             "unet_conv_tflops": round(tf, 1), "unet_conv_frac_of_bf16_peak": round(tf / peaks_bf16, 4),
             "unet_train_step_ms_16_crops": round(1e3 * t_train, 3),
             "note": "3x3 convolutions (forward, data and weight gradients) run on tcgen05 BF16 MMAs with float32 accumulators in tensor memory, operands loaded by TMA"}
@@ -649,9 +822,11 @@ def bench_image(args, dev, flush, ws, c2):
     stream = torch.cuda.current_stream()
     vis = torch.empty(c2["W"] ** 2, dtype=torch.uint8, device=dev)
 
+    vis4 = [torch.empty(c2["W"] ** 2, dtype=torch.uint8, device=dev) for _ in cams]
+
     def one():
-        for cam, (f, sg) in zip(cams, imgs):
-            m.fuse_image(cam.H, cam.Wi, cam.K, cam.T, [(f, [0, 3]), (sg, [1, 2])], vis=vis)
+        for cam, (f, sg), v in zip(cams, imgs, vis4):
+            m.fuse_image(cam.H, cam.Wi, cam.K, cam.T, [(f, [0, 3]), (sg, [1, 2])], vis=v)
 
     for _ in range(2):
         one()
@@ -667,10 +842,29 @@ def bench_image(args, dev, flush, ws, c2):
         tot += a.elapsed_time(b) / 1e3
     m.check()
     t = max_over_ranks(tot / reps, ws)
-    nvis = int(vis.sum().item())
+    nvis = [int(v.sum().item()) for v in vis4]
+    # kernel time per camera (event pairs around each launch)
+    m.set_profiling(True)
+    m.get_profile()
+    for i in range(reps):
+        flush(i)
+        one()
+    prof = m.get_profile()
+    m.set_profiling(False)
+    us_cam = 1e3 * prof["image"][0] / max(1, prof["image"][1])
+    # algorithmic bytes per camera: every cell's height and flags (projection), and per
+    # visible cell its pixel rows (64 + 20 float32) and the read + write of its layers
+    per_vis = (64 + 20) * 4 + (64 * 4 * 2 + 8) + (64 * 2 * 2 + 8) + 20 * 4 * 2 + 8 + 4
+    algo = float(np.mean(nvis)) * per_vis + c2["W"] ** 2 * 8
+    peak, _ = peaks()
     return {"workload": "4 cameras 848x480, 64-d F32 + 64-d BF16 Gaussian features, 20-class Dirichlet + class max, 500x500 map",
             "ms_per_4_cameras": round(1e3 * t, 4), "camera_fuses_per_s": round(ws * 4 / t, 1),
-            "cells_per_s": round(ws * 4 * c2["W"] ** 2 / t, 1), "visible_cells_last_camera": nvis}
+            "cells_per_s": round(ws * 4 * c2["W"] ** 2 / t, 1), "visible_cells_per_camera": nvis,
+            "roofline": {"kernel": "k_image", "bound": "hbm (pixel gather and layer read-modify-write); the "
+                                                        "visibility walks run from L1/L2",
+                         "us_per_launch": round(us_cam, 2), "algorithmic_bytes_per_launch": round(algo),
+                         "achieved": round(algo / (us_cam / 1e6) / 1e9, 1), "unit": "GB/s", "peak": peak,
+                         "frac": round(algo / (us_cam / 1e6) / 1e9 / peak, 4)}}
 
 
 # ----------------------------------------------------------------------------- CPU oracle
@@ -740,6 +934,9 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-image", action="store_true")
     ap.add_argument("--no-raycast", action="store_true")
+    ap.add_argument("--no-small", action="store_true")
+    ap.add_argument("--no-topk", action="store_true")
+    ap.add_argument("--no-plugins", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-inpaint", action="store_true")
     ap.add_argument("--inpaint-crops", type=int, default=256)

@@ -352,17 +352,19 @@ def config3(seed: int = 0, scale: float = 1.0, n_feat: int = 64):
 # configuration 4: 512 independent maps, log-uniform 5k..60k points, RGB + 16-d bf16 features
 
 
+def config4_cloud(b: int, seed_base: int = 10_000, n_lo: int = 5_000, n_hi: int = 60_000,
+                  W: int = 200, res: float = 0.05, n_feat: int = 16):
+    """The cloud of map b of the batched workload (its own terrain, pose and size)."""
+    rng = np.random.default_rng(seed_base + b)
+    n = int(math.floor(math.exp(rng.uniform(math.log(n_lo), math.log(n_hi)))))
+    ter = Terrain.from_seed(seed_base + b)
+    sxy = tuple(rng.uniform(-1.0, 1.0, size=2))
+    return uniform_ground_cloud(seed_base + b + 500_000, n, W * res, ter, sensor_xy=sxy, n_feat=n_feat)
+
+
 def config4(n_maps: int = 512, seed_base: int = 10_000, n_lo: int = 5_000, n_hi: int = 60_000,
             W: int = 200, res: float = 0.05, n_feat: int = 16):
-    clouds = []
-    for b in range(n_maps):
-        rng = np.random.default_rng(seed_base + b)
-        n = int(math.floor(math.exp(rng.uniform(math.log(n_lo), math.log(n_hi)))))
-        ter = Terrain.from_seed(seed_base + b)
-        sxy = tuple(rng.uniform(-1.0, 1.0, size=2))
-        cl = uniform_ground_cloud(seed_base + b + 500_000, n, W * res, ter, sensor_xy=sxy,
-                                  n_feat=n_feat)
-        clouds.append(cl)
+    clouds = [config4_cloud(b, seed_base, n_lo, n_hi, W, res, n_feat) for b in range(n_maps)]
     offsets = np.zeros(n_maps + 1, dtype=np.int64)
     offsets[1:] = np.cumsum([c.n for c in clouds])
     return dict(W=W, res=res, clouds=clouds, offsets=offsets)

@@ -121,3 +121,26 @@ def test_batched_with_empty_maps(torch):
         o = O.OracleMap(O.Params(W=c["W"], res=c["res"], layers=[O.Layer(3, O.LATEST), O.Layer(16, O.GAUSS, store=O.BF16)]))
         o.fuse_points(cl.xyz, cl.T, [(cl.rgb, [0]), ((cl.feat,), [1])])
         compare_states(gpu_state(g, b), o, what=f"map {b}")
+
+
+@pytest.mark.parametrize("radix_bits", [8, 9])
+def test_batched_full_size_equals_per_map_oracle(torch, radix_bits):
+    """The bench's own batched workload at full size -- 512 maps of 200 x 200, 10.85 M points
+    (log-uniform 5k-60k per map), RGB average + 16-d BF16 Gaussian features, 25-bit keys -- in
+    one batched call with 3 or 4 radix passes; every map compared with its own oracle map
+    (integers bit-exact, floats at 1e-5, BF16 at one storage ulp)."""
+    B = 512
+    c = synth.config4(n_maps=B)
+    xyz, rgb, feat, _, T = synth.concat_clouds(c["clouds"])
+    assert int(c["offsets"][-1]) > 10_000_000
+    layers = [dict(channels=3, rule=O.LATEST), dict(channels=16, rule=O.GAUSS, dtype=O.BF16)]
+    g, _ = make_pair(c["W"], c["res"], layers, n_maps=B, max_points=int(c["offsets"][-1]) + 4096)
+    g.set_tuning(radix_bits, 4)
+    assert g.get_tuning()["passes"] == (4 if radix_bits == 8 else 3)
+    g.fuse_pointcloud_batch(c["offsets"], torch.from_numpy(xyz).cuda(), T, _batch_sources(torch, rgb, feat))
+    g.check()
+    for b, cl in enumerate(c["clouds"]):
+        o = O.OracleMap(O.Params(W=c["W"], res=c["res"],
+                                 layers=[O.Layer(3, O.LATEST), O.Layer(16, O.GAUSS, store=O.BF16)]))
+        o.fuse_points(cl.xyz, cl.T, [(cl.rgb, [0]), ((cl.feat,), [1])])
+        compare_states(gpu_state(g, b), o, what=f"map {b}")
