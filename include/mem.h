@@ -347,7 +347,10 @@ mem_status mem_pca_layer(mem_map *m, int32_t map_index, int32_t layer, int32_t n
  * border) -- the discrete Laplace equation with the known cells as boundary
  * values; known cells are copied. Solved in float32 by red-black successive
  * over-relaxation from the mean of the crop's known cells, until the largest
- * update of a sweep is below tol or after max_iters sweeps.
+ * update of a sweep is below tol or after max_iters sweeps. A crop whose rows
+ * fit the shared memory of a thread-block cluster of up to 8 CTAs is solved
+ * there (rows split over the cluster, the rows next to a CTA's band read from
+ * the neighbouring CTAs' shared memory); larger crops in global memory.
  *   h_in, h_out  device float32 [n_crops][H][W] (may not alias)
  *   known        device uint8 [n_crops][H][W]
  *   iters_out    device int32 [n_crops] sweeps used (optional)

@@ -2,15 +2,19 @@
 // mean of its in-crop 4-neighbours (zero-flux border), known cells stay fixed,
 // i.e. the discrete Laplace equation with the known cells as boundary values.
 //
-// One thread block owns one crop, so the red-black successive
-// over-relaxation sweeps only need block barriers; a crop of 256 x 256 float32
-// values is 256 KB, and a batch of them stays resident in the 129 MB L2.
+// A crop that fits the shared memory of a cluster of up to 8 CTAs is solved by
+// k_inpaint_sor_cluster (its rows split over the cluster, boundary rows read
+// from the neighbours' shared memory); larger crops by k_inpaint_sor, one
+// thread block per crop working in global memory (L2-resident).
 // Unknown cells start from the mean of the crop's known cells; the sweeps stop
 // when the largest update of a full sweep falls below `tol` or after
 // `max_iters` sweeps.
+#include <cooperative_groups.h>
 #include <math.h>
 
 #include "mem_host.h"
+
+namespace cg = cooperative_groups;
 
 namespace memk {
 
@@ -104,7 +108,215 @@ __global__ void __launch_bounds__(kInpThreads) k_inpaint_sor(int H, int W, const
   if (threadIdx.x == 0 && iters_out) iters_out[blockIdx.x] = it;
 }
 
+// The same red-black SOR with the crop held in shared memory: a thread-block
+// cluster of CL CTAs owns one crop, CTA r its band of rows [r H / CL,
+// (r + 1) H / CL) with their known flags; the rows just above and below a band
+// are read from the neighbouring CTAs' shared memory (distributed shared
+// memory) after a cluster barrier. Every CTA adds the CTAs' partial sums (mean
+// of the known heights) and maxima (largest update of a sweep) in rank order,
+// so all of them take the same decisions and leave the loop together.
+//
+// Each colour is stored packed: cell (x, y) of colour c = (x + y) & 1 sits at
+// index k = x >> 1 of row y of array c. With p = (y + c) & 1 (so x = 2k + p), its
+// four neighbours (colour 1 - c) are k - 1 + p and k + p of the same row and k
+// of the rows above and below, so a warp's lanes read consecutive words. The
+// mask byte of a cell holds bit 0 = known and bit 1 = at the left or right
+// crop edge (fewer than four neighbours): interior rows update four cells per
+// lane where the byte is 0 and redo the edge cell of the row on its own.
+constexpr int kSorSmemMax = 220 * 1024;
+
+template <int P>
+__device__ __forceinline__ void sor_row_vec(float* crow, const float* orow, const float* oup, const float* odn,
+                                            const uint8_t* krow, int Wh, float omega, float& dmax) {
+  const int lane = threadIdx.x & 31;
+  for (int k0 = 4 * lane; k0 < Wh; k0 += 128) {
+    const float4 c4 = *reinterpret_cast<const float4*>(crow + k0);
+    const float4 o4 = *reinterpret_cast<const float4*>(orow + k0);
+    const float4 u4 = *reinterpret_cast<const float4*>(oup + k0);
+    const float4 d4 = *reinterpret_cast<const float4*>(odn + k0);
+    const uint32_t kk = *reinterpret_cast<const uint32_t*>(krow + k0);
+    // the fifth neighbour value of the four cells (never used for an edge cell)
+    const float side = P ? (k0 + 4 < Wh ? orow[k0 + 4] : 0.f) : (k0 > 0 ? orow[k0 - 1] : 0.f);
+    const float lft[4] = {P ? o4.x : side, P ? o4.y : o4.x, P ? o4.z : o4.y, P ? o4.w : o4.z};
+    const float rgt[4] = {P ? o4.y : o4.x, P ? o4.z : o4.y, P ? o4.w : o4.z, P ? side : o4.w};
+    const float uv[4] = {u4.x, u4.y, u4.z, u4.w}, dv[4] = {d4.x, d4.y, d4.z, d4.w};
+    float cv[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float d = (((lft[j] + rgt[j]) + uv[j]) + dv[j]) * 0.25f - cv[j];  // x 0.25 = / 4 exactly
+      if (((kk >> (8 * j)) & 0xffu) == 0u) {
+        cv[j] = fmaf(omega, d, cv[j]);
+        dmax = fmaxf(dmax, fabsf(d));
+      }
+    }
+    *reinterpret_cast<float4*>(crow + k0) = make_float4(cv[0], cv[1], cv[2], cv[3]);
+  }
+}
+
+// one cell by the general rule (any neighbour count)
+__device__ __forceinline__ void sor_cell(float* crow, const float* orow, const float* oup, const float* odn, int k,
+                                         int p, int W, float omega, float& dmax) {
+  const int x = 2 * k + p;
+  float sum = 0.f;
+  int m = 0;
+  if (x > 0) sum += orow[k - 1 + p], ++m;
+  if (x + 1 < W) sum += orow[k + p], ++m;
+  if (oup) sum += oup[k], ++m;
+  if (odn) sum += odn[k], ++m;
+  if (m == 0) return;  // a 1 x 1 crop keeps its starting value
+  const float old = crow[k];
+  const float d = (m == 4 ? sum * 0.25f : sum / (float)m) - old;
+  crow[k] = fmaf(omega, d, old);
+  dmax = fmaxf(dmax, fabsf(d));
+}
+
+__global__ void __launch_bounds__(kInpThreads) k_inpaint_sor_cluster(int H, int W, int CL,
+                                                                     const float* __restrict__ hin,
+                                                                     const uint8_t* __restrict__ known,
+                                                                     float* __restrict__ hout, float omega, float tol,
+                                                                     int max_iters, int* iters_out) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int r = (int)cl.block_rank();
+  const int crop = blockIdx.x / CL;
+  const int y0 = (int)((int64_t)H * r / CL), y1 = (int)((int64_t)H * (r + 1) / CL);
+  const int rows = y1 - y0;
+  const int rows_max = (H + CL - 1) / CL;
+  const int Wh = (W + 1) / 2;
+  extern __shared__ float sh[];
+  float* A[2] = {sh, sh + (size_t)rows_max * Wh};  // [colour][rows_max][Wh]
+  uint8_t* Kn = (uint8_t*)(sh + 2 * (size_t)rows_max * Wh);
+  uint8_t* K[2] = {Kn, Kn + (size_t)rows_max * Wh};
+  __shared__ float red[33];
+  __shared__ float s_part[2];
+  __shared__ float s_dm[2];
+  __shared__ int s_ne[2];
+  // border cells of the crop (fewer than four neighbours) per colour, as ly << 16 | k
+  u32* elist[2] = {(u32*)(Kn + ((2 * (size_t)rows_max * Wh + 3) & ~(size_t)3)), nullptr};
+  const int ecap = 2 * rows_max + 2 * Wh + 2;  // one or two edge cells per row, the first and last rows
+  elist[1] = elist[0] + ecap;
+  if (threadIdx.x < 2) s_ne[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)crop * H * W + (int64_t)y0 * W;
+  float s = 0.f, c = 0.f;
+  for (int j = threadIdx.x; j < rows * W; j += blockDim.x) {
+    const int ly = j / W, x = j - ly * W;
+    const int y = y0 + ly;
+    const int col = (x + y) & 1;
+    const uint8_t k = known[base + j];
+    const float v = hin[base + j];
+    const bool border = x == 0 || x == W - 1 || y == 0 || y == H - 1;
+    K[col][ly * Wh + (x >> 1)] = (uint8_t)((k ? 1 : 0) | (border ? 2 : 0));
+    A[col][ly * Wh + (x >> 1)] = v;
+    if (border && !k) elist[col][atomicAdd(&s_ne[col], 1)] = ((u32)ly << 16) | (u32)(x >> 1);
+    if (k) {
+      s += v;
+      c += 1.f;
+    }
+  }
+  s = block_sum(s, red);
+  c = block_sum(c, red);
+  if (threadIdx.x == 0) {
+    s_part[0] = s;
+    s_part[1] = c;
+  }
+  cl.sync();
+  float S = 0.f, Cn = 0.f;
+  for (int q = 0; q < CL; ++q) {
+    const float* pp = cl.map_shared_rank(s_part, q);
+    S += pp[0];
+    Cn += pp[1];
+  }
+  const float mean = Cn > 0.f ? S / Cn : 0.f;
+  for (int q = 0; q < 2; ++q)
+    for (int j = threadIdx.x; j < rows * Wh; j += blockDim.x)
+      if (!(K[q][j] & 1)) A[q][j] = mean;
+  // the neighbouring bands' boundary rows, per colour: the last row of CTA r - 1, the first of CTA r + 1
+  const int rows_prev = r > 0 ? y0 - (int)((int64_t)H * (r - 1) / CL) : 0;
+  const float* up_row[2] = {nullptr, nullptr};
+  const float* dn_row[2] = {nullptr, nullptr};
+  for (int q = 0; q < 2; ++q) {
+    if (r > 0) up_row[q] = cl.map_shared_rank(A[q], r - 1) + (size_t)(rows_prev - 1) * Wh;
+    if (r + 1 < CL) dn_row[q] = cl.map_shared_rank(A[q], r + 1);
+  }
+  cl.sync();
+  const bool vec = (W & 1) == 0 && (Wh & 3) == 0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  int it = 0;
+  for (; it < max_iters; ++it) {
+    float dmax = 0.f;
+    for (int color = 0; color < 2; ++color) {
+      const float* O = A[1 - color];
+      if (vec) {
+        // every row through the branch-free path (a border cell's mask byte is not 0, so the
+        // row above the crop's first row, or below its last, is never used: the row itself
+        // stands in for it), then the crop's border cells of this colour from the list
+        for (int ly = warp; ly < rows; ly += nwarps) {
+          const int y = y0 + ly;
+          const float* orow = O + (size_t)ly * Wh;
+          const float* oup = y > 0 ? (ly > 0 ? orow - Wh : up_row[1 - color]) : orow;
+          const float* odn = y + 1 < H ? (ly + 1 < rows ? orow + Wh : dn_row[1 - color]) : orow;
+          if ((y + color) & 1)
+            sor_row_vec<1>(A[color] + (size_t)ly * Wh, orow, oup, odn, K[color] + (size_t)ly * Wh, Wh, omega, dmax);
+          else
+            sor_row_vec<0>(A[color] + (size_t)ly * Wh, orow, oup, odn, K[color] + (size_t)ly * Wh, Wh, omega, dmax);
+        }
+        for (int e = threadIdx.x; e < s_ne[color]; e += blockDim.x) {
+          const u32 v = elist[color][e];
+          const int ly = (int)(v >> 16), k = (int)(v & 0xffffu);
+          const int y = y0 + ly;
+          const float* orow = O + (size_t)ly * Wh;
+          const float* oup = y > 0 ? (ly > 0 ? orow - Wh : up_row[1 - color]) : nullptr;
+          const float* odn = y + 1 < H ? (ly + 1 < rows ? orow + Wh : dn_row[1 - color]) : nullptr;
+          sor_cell(A[color] + (size_t)ly * Wh, orow, oup, odn, k, (y + color) & 1, W, omega, dmax);
+        }
+      } else {
+        for (int ly = warp; ly < rows; ly += nwarps) {
+          const int y = y0 + ly;
+          const int p = (y + color) & 1;
+          const float* orow = O + (size_t)ly * Wh;
+          const float* oup = y > 0 ? (ly > 0 ? orow - Wh : up_row[1 - color]) : nullptr;
+          const float* odn = y + 1 < H ? (ly + 1 < rows ? orow + Wh : dn_row[1 - color]) : nullptr;
+          const uint8_t* krow = K[color] + (size_t)ly * Wh;
+          for (int k = lane; 2 * k + p < W; k += 32)
+            if (!(krow[k] & 1)) sor_cell(A[color] + (size_t)ly * Wh, orow, oup, odn, k, p, W, omega, dmax);
+        }
+      }
+      if (color == 1) {  // the sweep's largest update, published with the barrier below
+        dmax = block_max(dmax, red);
+        if (threadIdx.x == 0) s_dm[it & 1] = dmax;
+      }
+      cl.sync();  // this colour's values (and the sweep's maximum) are final for every CTA
+    }
+    // s_dm[it & 1] is next written two sweeps later, after two more cluster barriers
+    float gmax = 0.f;
+    for (int q = 0; q < CL; ++q) gmax = fmaxf(gmax, cl.map_shared_rank(s_dm, q)[it & 1]);
+    if (gmax < tol) {
+      ++it;
+      break;
+    }
+  }
+  for (int j = threadIdx.x; j < rows * W; j += blockDim.x) {
+    const int ly = j / W, x = j - ly * W;
+    hout[base + j] = A[(x + y0 + ly) & 1][ly * Wh + (x >> 1)];
+  }
+  if (r == 0 && threadIdx.x == 0 && iters_out) iters_out[crop] = it;
+  cl.sync();  // no CTA leaves while another may still read its shared memory
+}
+
 }  // namespace memk
+
+static size_t sor_smem(int H, int W, int cl) {
+  const int64_t rows = (H + cl - 1) / cl, wh = (W + 1) / 2;
+  return (size_t)rows * wh * 2 * 5 + (size_t)2 * 4 * (2 * rows + 2 * wh + 2) + 16;  // + border lists
+}
+// cluster size for a crop held in shared memory: the fewest CTAs (1..8) whose bands of rows
+// (heights and mask bytes) fit kSorSmemMax (fewer CTAs: fewer rows read across CTAs and
+// cheaper cluster barriers; measured faster than two CTAs per SM); 0 when none does
+static int sor_cluster_size(int H, int W) {
+  for (int cl = 1; cl <= 8 && cl <= H; ++cl)
+    if (sor_smem(H, W, cl) <= (size_t)memk::kSorSmemMax) return cl;
+  return 0;
+}
 
 extern "C" mem_status mem_inpaint_diffusion(int32_t n_crops, int32_t H, int32_t W, const float* h_in,
                                             const uint8_t* known, float* h_out, float tol,
@@ -117,9 +329,38 @@ extern "C" mem_status mem_inpaint_diffusion(int32_t n_crops, int32_t H, int32_t 
   // optimal over-relaxation of the model problem on the longer side
   const int L = H > W ? H : W;
   const float omega = (float)(2.0 / (1.0 + sin(M_PI / (double)(L + 1))));
-  memk::k_inpaint_sor<<<n_crops, memk::kInpThreads, 0, (cudaStream_t)stream>>>(
-      H, W, h_in, known, h_out, omega, tol, max_iters, iters_out);
-  cudaError_t e = cudaGetLastError();
+  const int CL = sor_cluster_size(H, W);
+  cudaError_t e = cudaSuccess;
+  if (CL > 0) {
+    const size_t smem = sor_smem(H, W, CL);
+    static bool attr[128] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 128 && !attr[dev]) {
+      e = cudaFuncSetAttribute(memk::k_inpaint_sor_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               memk::kSorSmemMax);
+      if (e != cudaSuccess) return memh::api_cuda_fail(e, "inpaint attribute");
+      attr[dev] = true;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(n_crops * CL));
+    cfg.blockDim = dim3(memk::kInpThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = (cudaStream_t)stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)CL;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, memk::k_inpaint_sor_cluster, H, W, CL, h_in, known, h_out, omega, tol,
+                           max_iters, iters_out);
+  } else {
+    memk::k_inpaint_sor<<<n_crops, memk::kInpThreads, 0, (cudaStream_t)stream>>>(
+        H, W, h_in, known, h_out, omega, tol, max_iters, iters_out);
+    e = cudaGetLastError();
+  }
   if (e != cudaSuccess) return memh::api_cuda_fail(e, "inpaint launch");
   return MEM_OK;
 }
