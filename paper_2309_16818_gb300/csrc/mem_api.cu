@@ -515,6 +515,7 @@ extern "C" mem_status mem_destroy_map(mem_map* mm) {
   }
   if (m->copy_stream) cudaStreamDestroy(m->copy_stream);
   if (m->pca_buf) cudaFree(m->pca_buf);
+  for (cudaEvent_t e : m->prof_pool) cudaEventDestroy(e);
   delete mm;
   return MEM_OK;
 }
@@ -1063,10 +1064,9 @@ extern "C" mem_status mem_get_profile(mem_map* mm, double ms[MEM_PROFILE_SLOTS],
     CK(cudaEventElapsedTime(&t, p.a, p.b), "profile elapsed");
     m->prof_ms[p.slot] += t;
     m->prof_calls[p.slot] += 1;
-    cudaEventDestroy(p.a);
-    cudaEventDestroy(p.b);
   }
   m->prof_pending.clear();
+  m->prof_next = 0;  // every pooled event is free again
   for (int k = 0; k < MEM_PROFILE_SLOTS; ++k) {
     ms[k] = k < 16 ? m->prof_ms[k] : 0.0;
     calls[k] = k < 16 ? m->prof_calls[k] : 0;

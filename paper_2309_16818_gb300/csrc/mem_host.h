@@ -44,6 +44,8 @@ struct Map {
     cudaEvent_t a, b;
   };
   std::vector<ProfMark> prof_pending;
+  std::vector<cudaEvent_t> prof_pool;  // events of the pending marks, reused after each read
+  size_t prof_next = 0;
   double prof_ms[16] = {};
   int64_t prof_calls[16] = {};
   // host-buffer fuse: two device staging buffers used in turn, filled on a
@@ -66,25 +68,32 @@ struct Map {
 enum { kProfKey = 0, kProfDigits, kProfSort, kProfUnused3, kProfFuseTiles, kProfFuseCross,
        kProfTime, kProfImage, kProfMove, kProfDrift, kProfRay, kProfSlots };
 
-// Brackets a launch group with events when profiling is on.
+// Brackets a launch group with events when profiling is on. Events come from a
+// pool the map keeps (created on first use, reused after each read of the
+// profile), so recording costs no event creation between the launches.
+inline cudaEvent_t prof_event(Map* m) {
+  if (m->prof_next < m->prof_pool.size()) return m->prof_pool[m->prof_next++];
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  m->prof_pool.push_back(e);
+  ++m->prof_next;
+  return e;
+}
+
 struct ProfScope {
   Map* m;
   int slot;
   cudaStream_t st;
   cudaEvent_t a = nullptr;
   ProfScope(Map* m_, int slot_, cudaStream_t st_) : m(m_), slot(slot_), st(st_) {
-    if (m->prof_on) {
-      cudaEventCreate(&a);
-      cudaEventRecord(a, st);
-    }
+    if (m->prof_on && (a = prof_event(m)) != nullptr) cudaEventRecord(a, st);
   }
   ~ProfScope() {
-    if (a) {
-      cudaEvent_t b;
-      cudaEventCreate(&b);
-      cudaEventRecord(b, st);
-      m->prof_pending.push_back({slot, a, b});
-    }
+    if (!a) return;
+    cudaEvent_t b = prof_event(m);
+    if (!b) return;
+    cudaEventRecord(b, st);
+    m->prof_pending.push_back({slot, a, b});
   }
 };
 

@@ -4,10 +4,11 @@
 // strictly below the ray from the camera to the cell (equality occludes).
 // Visible cells fuse their pixel with the layer rules (one observation).
 //
-// One thread per cell walks its own line (16x16 cell tiles, so neighbouring
-// threads read neighbouring heights through L1); the warp then fuses the
-// visible cells one at a time with its lanes spread over the channels, so
-// pixel rows and layer rows are read and written coalesced.
+// A 16x16 tile of cells per block: the cells that need a visibility walk are
+// listed in shared memory and walked by consecutive threads (neighbouring
+// cells, so neighbouring lines read neighbouring heights through L1); each warp
+// then fuses its visible cells one at a time with its lanes spread over the
+// channels, so pixel rows and layer rows are read and written coalesced.
 #include "mem_host.h"
 
 namespace memk {
@@ -34,34 +35,70 @@ __device__ __forceinline__ u32 phys(const MapDev& md, int rx, int ry, int x, int
 // Walk the integer Bresenham line from the camera cell (sx, sy) to (ex, ey)
 // and test every intermediate cell against the ray height
 //   ray = h_cam + t (h_cell - h_cam),  t = ((q - s).(e - s)) / |e - s|^2.
+// Four cells per step with their loads issued together; the ray height is
+// first estimated with a reciprocal of |e - s|^2 (relative error of t below
+// 2^-22), and only where the estimate lies within a bound of the cell's
+// height is the exact sequence (correctly rounded division, fma) taken, so
+// every decision equals the exact one. Stops at the first occluder.
 __device__ __forceinline__ bool walk_visible(const MapDev& md, u32 base, int rx, int ry, int sx, int sy,
                                              int ex, int ey, float hz, float hc) {
   const int dx = abs(ex - sx), dy = -abs(ey - sy);
   const int stx = sx < ex ? 1 : -1, sty = sy < ey ? 1 : -1;
   const int dxs = ex - sx, dys = ey - sy;
   const float den = (float)(dxs * dxs + dys * dys);
+  const float rden = __frcp_rn(den);
   const float dh = __fsub_rn(hz, hc);
+  const float tol = 4e-6f * (fabsf(dh) + fabsf(hc) + 1.f);
   int err = dx + dy, x = sx, y = sy;
-  if (x == ex && y == ey) return true;
-  for (;;) {
-    const int e2 = 2 * err;
-    if (e2 >= dy) {
-      err += dy;
-      x += stx;
+  bool done = (x == ex && y == ey);
+  while (!done) {
+    int qx[4], qy[4];
+    bool act[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      act[u] = false;
+      qx[u] = qy[u] = 0;
+      if (!done) {
+        const int e2 = 2 * err;
+        if (e2 >= dy) {
+          err += dy;
+          x += stx;
+        }
+        if (e2 <= dx) {
+          err += dx;
+          y += sty;
+        }
+        if (x == ex && y == ey) {
+          done = true;
+        } else {
+          qx[u] = x;
+          qy[u] = y;
+          act[u] = true;
+        }
+      }
     }
-    if (e2 <= dx) {
-      err += dx;
-      y += sty;
+    u32 fl[4];
+    float hq[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const u32 q = base + phys(md, rx, ry, qx[u], qy[u]);
+      fl[u] = act[u] ? md.flags[q] : 0u;
+      hq[u] = act[u] ? __ldg(md.h + q) : 0.f;
     }
-    if (x == ex && y == ey) return true;
-    const u32 q = base + phys(md, rx, ry, x, y);
-    if (__ldg(md.flags + q) & kFlagValid) {
-      const int num = (x - sx) * dxs + (y - sy) * dys;
-      const float tq = __fdiv_rn((float)num, den);
-      const float ray = __fmaf_rn(tq, dh, hc);
-      if (__ldg(md.h + q) >= ray) return false;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (!act[u] || !(fl[u] & kFlagValid)) continue;
+      const int num = (qx[u] - sx) * dxs + (qy[u] - sy) * dys;
+      const float est = hq[u] - __fmaf_rn(__fmul_rn((float)num, rden), dh, hc);
+      bool occ = est > 0.f;
+      if (fabsf(est) <= tol + 4e-6f * fabsf(hq[u])) {  // near the ray: the exact sequence
+        const float tq = __fdiv_rn((float)num, den);
+        occ = hq[u] >= __fmaf_rn(tq, dh, hc);
+      }
+      if (occ) return false;
     }
   }
+  return true;
 }
 
 // Fuse pixel p into cell g with the whole warp (lanes over channels).
@@ -114,50 +151,81 @@ __device__ __forceinline__ void fuse_pixel_warp(const MapDev& md, const ImgParam
   if (lane == 0) md.flags[g] = fl;
 }
 
+// A block takes a 16 x 16 tile of cells: every thread projects its cell, the
+// cells that are valid, in front of the camera and inside the image are listed
+// in shared memory, and consecutive threads walk the listed cells' lines (the
+// others are done); each warp then fuses its visible cells' pixels.
 __global__ void __launch_bounds__(256) k_image(MapDev md, ImgParams ip, uint8_t* __restrict__ vis,
                                                int32_t* __restrict__ pix) {
   const int W = md.W;
-  const int ix = blockIdx.x * 16 + threadIdx.x;
-  const int iy = blockIdx.y * 16 + threadIdx.y;
-  const bool inside = ix < W && iy < W;
+  const int tid = threadIdx.y * 16 + threadIdx.x;
   const u32 base = (u32)ip.map_index * md.W2;
-  bool visible = false;
-  int64_t g = 0, p = -1;
-  u32 fl = 0;
-  if (inside) {
-    g = base + phys(md, ip.ring_x, ip.ring_y, ix, iy);
-    fl = md.flags[g];
-    if (fl & kFlagValid) {
-      const float xc = __fmul_rn(__fadd_rn((float)(ix - W / 2), 0.5f), md.res);
-      const float yc = __fmul_rn(__fadd_rn((float)(iy - W / 2), 0.5f), md.res);
-      const float hz = md.h[g];
-      const float Xc = __fmaf_rn(ip.R[0], xc, __fmaf_rn(ip.R[1], yc, __fmaf_rn(ip.R[2], hz, ip.t[0])));
-      const float Yc = __fmaf_rn(ip.R[3], xc, __fmaf_rn(ip.R[4], yc, __fmaf_rn(ip.R[5], hz, ip.t[1])));
-      const float Zc = __fmaf_rn(ip.R[6], xc, __fmaf_rn(ip.R[7], yc, __fmaf_rn(ip.R[8], hz, ip.t[2])));
-      if (Zc > md.z_near) {
-        const float u = __fmaf_rn(ip.fx, __fdiv_rn(Xc, Zc), ip.cx);
-        const float v = __fmaf_rn(ip.fy, __fdiv_rn(Yc, Zc), ip.cy);
-        const float fu = floorf(__fadd_rn(u, 0.5f));
-        const float fv = floorf(__fadd_rn(v, 0.5f));
-        if (fu >= 0.f && fu < (float)ip.Wi && fv >= 0.f && fv < (float)ip.H) {
-          visible = walk_visible(md, base, ip.ring_x, ip.ring_y, ip.sx, ip.sy, ix, iy, hz, ip.hc);
-          if (visible) p = (int64_t)fv * ip.Wi + (int64_t)fu;
+  __shared__ int s_n;
+  __shared__ u32 s_cell[256];
+  __shared__ float s_hz[256];
+  __shared__ int32_t s_pix[256];
+  if (tid == 0) s_n = 0;
+  __syncthreads();
+  {
+    const int ix = blockIdx.x * 16 + threadIdx.x;
+    const int iy = blockIdx.y * 16 + threadIdx.y;
+    if (ix < W && iy < W) {
+      const u32 g = base + phys(md, ip.ring_x, ip.ring_y, ix, iy);
+      bool listed = false;
+      if (md.flags[g] & kFlagValid) {
+        const float xc = __fmul_rn(__fadd_rn((float)(ix - W / 2), 0.5f), md.res);
+        const float yc = __fmul_rn(__fadd_rn((float)(iy - W / 2), 0.5f), md.res);
+        const float hz = md.h[g];
+        const float Xc = __fmaf_rn(ip.R[0], xc, __fmaf_rn(ip.R[1], yc, __fmaf_rn(ip.R[2], hz, ip.t[0])));
+        const float Yc = __fmaf_rn(ip.R[3], xc, __fmaf_rn(ip.R[4], yc, __fmaf_rn(ip.R[5], hz, ip.t[1])));
+        const float Zc = __fmaf_rn(ip.R[6], xc, __fmaf_rn(ip.R[7], yc, __fmaf_rn(ip.R[8], hz, ip.t[2])));
+        if (Zc > md.z_near) {
+          const float u = __fmaf_rn(ip.fx, __fdiv_rn(Xc, Zc), ip.cx);
+          const float v = __fmaf_rn(ip.fy, __fdiv_rn(Yc, Zc), ip.cy);
+          const float fu = floorf(__fadd_rn(u, 0.5f));
+          const float fv = floorf(__fadd_rn(v, 0.5f));
+          if (fu >= 0.f && fu < (float)ip.Wi && fv >= 0.f && fv < (float)ip.H) {
+            const int k = atomicAdd(&s_n, 1);
+            s_cell[k] = ((u32)iy << 16) | (u32)ix;
+            s_hz[k] = hz;
+            s_pix[k] = (int32_t)((int64_t)fv * ip.Wi + (int64_t)fu);
+            listed = true;
+          }
         }
       }
+      if (!listed) {
+        const int64_t j = (int64_t)iy * W + ix;
+        if (vis) vis[j] = 0;
+        if (pix) pix[j] = -1;
+      }
     }
+  }
+  __syncthreads();
+  const int n = s_n;
+  __shared__ int s_nv;
+  __shared__ u32 s_vg[256];
+  __shared__ int32_t s_vp[256];
+  if (tid == 0) s_nv = 0;
+  __syncthreads();
+  if (tid < n) {
+    const int ix = (int)(s_cell[tid] & 0xffffu), iy = (int)(s_cell[tid] >> 16);
+    const bool visible = walk_visible(md, base, ip.ring_x, ip.ring_y, ip.sx, ip.sy, ix, iy, s_hz[tid], ip.hc);
     const int64_t j = (int64_t)iy * W + ix;
     if (vis) vis[j] = visible ? 1 : 0;
-    if (pix) pix[j] = visible ? (int32_t)p : -1;
+    if (pix) pix[j] = visible ? s_pix[tid] : -1;
+    if (visible && ip.n_src > 0) {
+      const int k = atomicAdd(&s_nv, 1);
+      s_vg[k] = base + phys(md, ip.ring_x, ip.ring_y, ix, iy);
+      s_vp[k] = s_pix[tid];
+    }
   }
   if (ip.n_src == 0) return;
-  u32 m = __ballot_sync(0xffffffffu, visible);
-  while (m) {
-    const int v = __ffs(m) - 1;
-    m &= m - 1;
-    const int64_t gv = __shfl_sync(0xffffffffu, g, v);
-    const int64_t pv = __shfl_sync(0xffffffffu, p, v);
-    const u32 flv = __shfl_sync(0xffffffffu, fl, v);
-    fuse_pixel_warp(md, ip, gv, pv, flv);
+  __syncthreads();
+  // the visible cells dealt out to the block's warps, each fused by a whole warp
+  const int warp = tid >> 5, nwarps = (blockDim.x * blockDim.y) >> 5;
+  for (int v = warp; v < s_nv; v += nwarps) {
+    const u32 gv = s_vg[v];
+    fuse_pixel_warp(md, ip, gv, s_vp[v], md.flags[gv]);
   }
 }
 

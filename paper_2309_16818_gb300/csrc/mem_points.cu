@@ -851,7 +851,7 @@ __device__ __forceinline__ void tile_rule(const SumSmem& s, const LayerDev& L, i
 #undef MEM_TR
 }
 
-__global__ void __launch_bounds__(kFT, 6) k_fuse_tiles(MapDev md, const PointJob* __restrict__ job,
+__global__ void __launch_bounds__(kFT, 7) k_fuse_tiles(MapDev md, const PointJob* __restrict__ job,
                                                        int sorted1) {
   extern __shared__ __align__(16) unsigned char fz_raw[];
   SumSmem& s = *reinterpret_cast<SumSmem*>(fz_raw);
