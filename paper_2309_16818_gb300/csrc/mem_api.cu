@@ -717,6 +717,12 @@ static mem_status run_points(Map* m, int nm, const int64_t* offsets, int64_t n, 
     acc += src[q].C + 2 * src[q].has_classmax;  // channel sums, then (max value, class)
   }
   build_fuse_tables(*job, acc, m->cfg);
+  m->fuse_topk = 0;
+  for (int q = 0; q < n_src; ++q) m->fuse_topk |= src[q].topk ? 1 : 0;
+  if (m->graph && m->graph_topk != m->fuse_topk) {  // the graph launches the other kernel variant
+    cudaGraphExecDestroy(m->graph);
+    m->graph = nullptr;
+  }
   acc = (acc + 3) / 4 * 4;  // slots start on 16-byte boundaries (vector loads of their headers)
   job->acc = acc;
   {
@@ -763,6 +769,7 @@ static mem_status run_points(Map* m, int nm, const int64_t* offsets, int64_t n, 
       e = cudaGraphInstantiate(&m->graph, gph, 0);
       cudaGraphDestroy(gph);
       if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+      m->graph_topk = m->fuse_topk;
     }
     CK(cudaGraphLaunch(m->graph, st), "graph launch");
     return MEM_OK;

@@ -23,6 +23,8 @@ struct Map {
   int passes = 1;
   int key_bits = 1;
   uint32_t call_id = 0;  // point-path calls so far (the clean-up's per-cell stamps)
+  int fuse_topk = 0;      // the current point-path call has a top-k source (fuse kernel variant)
+  int graph_topk = -1;    // the variant the captured graph launches
   int n_sm = 148;
   int device = 0;
   std::vector<double> origin;  // [n_maps][2] world xy of each map centre

@@ -629,8 +629,9 @@ __device__ __forceinline__ void build_columns(SumSmem& s, int n_src, int r0, int
 }
 
 // four consecutive channels of a row (fewer at the end of the row)
+template <bool TOPK>
 __device__ __forceinline__ void ld_chunk(const ChunkDesc& d, int64_t row, float v[4]) {
-  if (d.topk) {  // expand the row's (class id, probability) pairs into the chunk's channels
+  if (TOPK && d.topk) {  // expand the row's (class id, probability) pairs into the chunk's channels
     const float* __restrict__ r = (const float*)d.data + row * 2 * d.topk;
 #pragma unroll
     for (int w = 0; w < 4; ++w) v[w] = 0.f;
@@ -851,6 +852,9 @@ __device__ __forceinline__ void tile_rule(const SumSmem& s, const LayerDev& L, i
 #undef MEM_TR
 }
 
+// TOPK: some source of the call has top-k rows; RAY: the map runs the ray-cast
+// clean-up (both known on the host, so the common call carries neither branch)
+template <bool TOPK, bool RAY>
 __global__ void __launch_bounds__(kFT, 7) k_fuse_tiles(MapDev md, const PointJob* __restrict__ job,
                                                        int sorted1) {
   extern __shared__ __align__(16) unsigned char fz_raw[];
@@ -868,8 +872,7 @@ __global__ void __launch_bounds__(kFT, 7) k_fuse_tiles(MapDev md, const PointJob
   const bool any_gauss = ft->any_gauss;  // Gaussian variances are written after every rule read them
   const float* __restrict__ xyz = job->xyz;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  const bool ray = md.ray_on != 0;
-  const u64 call_hi = (u64)job->call_id << 32;
+  const u64 call_hi = RAY ? (u64)job->call_id << 32 : 0ull;
   // the call's tables (built on the host) into shared memory
   if (t < n_src) s.src[t] = job->src[t];
   if (t < md.n_layers) s.L[t] = md.L[t];
@@ -1004,7 +1007,7 @@ __global__ void __launch_bounds__(kFT, 7) k_fuse_tiles(MapDev md, const PointJob
           float v[kStageU][4];
 #pragma unroll
           for (int u = 0; u < kStageU; ++u)
-            if (j0 + u < nck) ld_chunk(s.ck[j0 + u], row_i, v[u]);
+            if (j0 + u < nck) ld_chunk<TOPK>(s.ck[j0 + u], row_i, v[u]);
 #pragma unroll
           for (int u = 0; u < kStageU; ++u) {
             if (j0 + u < nck) {
@@ -1044,9 +1047,9 @@ __global__ void __launch_bounds__(kFT, 7) k_fuse_tiles(MapDev md, const PointJob
         row[1] = rej ? 0.f : z * w;
         row[2] = rej ? 0.f : 1.f;
         row[3] = rej ? 1.f : 0.f;
-        if (!rej) zk = call_hi | (u64)(~ordered_bits(__float_as_uint(z)));
+        if (RAY && !rej) zk = call_hi | (u64)(~ordered_bits(__float_as_uint(z)));
       }
-      if (ray && r0 == 0) {
+      if (RAY && r0 == 0) {
         // the lowest accepted z of every cell: a segmented max of the keys over each warp's
         // points (runs are contiguous), one atomic per run piece of the warp
         const int run = t < np ? s.pinf[t] >> 1 : -1;
@@ -1563,7 +1566,13 @@ static cudaError_t launch_rb(Map* m, const PointJob* d_job, cudaStream_t st) {
   {
     ProfScope ps(m, kProfFuseTiles, st);
     const int cps = g_sums_ctas_per_sm[current_device()];
-    k_fuse_tiles<<<sms * (cps > 0 ? cps : 1), kFT, sizeof(SumSmem), st>>>(md, d_job, P & 1);
+    const dim3 grid(sms * (cps > 0 ? cps : 1));
+    if (m->fuse_topk)
+      md.ray_on ? k_fuse_tiles<true, true><<<grid, kFT, sizeof(SumSmem), st>>>(md, d_job, P & 1)
+                : k_fuse_tiles<true, false><<<grid, kFT, sizeof(SumSmem), st>>>(md, d_job, P & 1);
+    else
+      md.ray_on ? k_fuse_tiles<false, true><<<grid, kFT, sizeof(SumSmem), st>>>(md, d_job, P & 1)
+                : k_fuse_tiles<false, false><<<grid, kFT, sizeof(SumSmem), st>>>(md, d_job, P & 1);
   }
   {
     ProfScope ps(m, kProfFuseCross, st);
@@ -1580,10 +1589,13 @@ static cudaError_t launch_rb(Map* m, const PointJob* d_job, cudaStream_t st) {
 
 cudaError_t prepare_kernels() {
   const int dev = current_device();
-  cudaError_t e = cudaFuncSetAttribute(k_fuse_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sizeof(SumSmem));
+  cudaError_t e = cudaSuccess;
+  for (auto f : {k_fuse_tiles<false, false>, k_fuse_tiles<false, true>, k_fuse_tiles<true, false>,
+                 k_fuse_tiles<true, true>})
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SumSmem));
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_sums_ctas_per_sm[dev], k_fuse_tiles, kFT, sizeof(SumSmem));
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_sums_ctas_per_sm[dev], k_fuse_tiles<false, false>, kFT,
+                                                      sizeof(SumSmem));
   if (g_sums_ctas_per_sm[dev] < 1) g_sums_ctas_per_sm[dev] = 1;
   if (e == cudaSuccess) e = set_attrs<8>();
   if (e == cudaSuccess) e = set_attrs<9>();
