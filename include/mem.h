@@ -269,16 +269,19 @@ mem_status mem_check(mem_map *m, void *stream);
 typedef enum { MEM_FAULT_NONE = 0, MEM_FAULT_SORT_WAIT = 1 } mem_fault;
 mem_status mem_inject_fault(mem_map *m, int32_t kind);
 
-/* Schedule of the point path (no effect on the results): radix_bits in
- * [8, 10] is the digit width of the key sort (at most 4 passes);
- * blocks_per_sm in [1, 32] sizes the persistent grids. Synchronises the
- * device. */
-mem_status mem_set_tuning(mem_map *m, int32_t radix_bits, int32_t blocks_per_sm);
-/* out = {radix_bits, blocks_per_sm, radix passes, 0} (host). */
+/* Schedule of the point path (results equal within float32 summation order;
+ * each schedule is deterministic): radix_bits in [8, 10] is the digit width
+ * of the key sort (at most 4 passes); blocks_per_sm in [1, 32] sizes the
+ * persistent grids; fuse_kernel 0 sums a call's per-cell quantities in
+ * registers, one point per lane (when its summed columns, 4 height sums plus
+ * every source's channels and arg-max pair, number at most 32), 1 always in
+ * shared-memory column walks over 128-point tiles. Synchronises the device. */
+mem_status mem_set_tuning(mem_map *m, int32_t radix_bits, int32_t blocks_per_sm, int32_t fuse_kernel);
+/* out = {radix_bits, blocks_per_sm, radix passes, fuse_kernel} (host). */
 mem_status mem_get_tuning(const mem_map *m, int32_t out[4]);
 
-/* Autotuner: times every schedule candidate (radix_bits in {8, 9, 10},
- * blocks_per_sm in {2, 4, 8}) on this batched call (arguments as for
+/* Autotuner: times every schedule candidate (fuse_kernel in {0, 1},
+ * radix_bits in {8, 9, 10}, blocks_per_sm in {2, 4, 8}) on this batched call (arguments as for
  * mem_fuse_pointcloud_batch), `reps` timed runs each from the same saved map
  * state, keeps the fastest and restores the state, so the map is unchanged.
  * Allocates a temporary copy of the map state. ms_out (host, optional) gets

@@ -520,15 +520,17 @@ extern "C" mem_status mem_destroy_map(mem_map* mm) {
   return MEM_OK;
 }
 
-extern "C" mem_status mem_set_tuning(mem_map* mm, int32_t radix_bits, int32_t blocks_per_sm) {
+extern "C" mem_status mem_set_tuning(mem_map* mm, int32_t radix_bits, int32_t blocks_per_sm, int32_t fuse_kernel) {
   if (!mm) return fail(MEM_ERR_ARG, "map is NULL");
   if (radix_bits < 8 || radix_bits > 10) return fail(MEM_ERR_ARG, "radix_bits in [8, 10]");
   if (blocks_per_sm < 1 || blocks_per_sm > 32) return fail(MEM_ERR_ARG, "blocks_per_sm in [1, 32]");
+  if (fuse_kernel < 0 || fuse_kernel > 1) return fail(MEM_ERR_ARG, "fuse_kernel is 0 or 1");
   Map* m = &mm->m;
   if ((m->key_bits + radix_bits - 1) / radix_bits > 4) return fail(MEM_ERR_ARG, "too many radix passes");
   cudaDeviceSynchronize();
   m->tune.radix_bits = radix_bits;
   m->tune.blocks_per_sm = blocks_per_sm;
+  m->tune.fuse_kernel = fuse_kernel;
   m->passes = (m->key_bits + radix_bits - 1) / radix_bits;
   if (m->passes > 4) return fail(MEM_ERR_ARG, "too many radix passes");
   if (m->graph) {
@@ -543,7 +545,7 @@ extern "C" mem_status mem_get_tuning(const mem_map* mm, int32_t out[4]) {
   out[0] = mm->m.tune.radix_bits;
   out[1] = mm->m.tune.blocks_per_sm;
   out[2] = mm->m.passes;
-  out[3] = 0;
+  out[3] = mm->m.tune.fuse_kernel;
   return MEM_OK;
 }
 
@@ -717,9 +719,9 @@ static mem_status run_points(Map* m, int nm, const int64_t* offsets, int64_t n, 
     acc += src[q].C + 2 * src[q].has_classmax;  // channel sums, then (max value, class)
   }
   build_fuse_tables(*job, acc, m->cfg);
-  m->fuse_topk = 0;
-  for (int q = 0; q < n_src; ++q) m->fuse_topk |= src[q].topk ? 1 : 0;
-  if (m->graph && m->graph_topk != m->fuse_topk) {  // the graph launches the other kernel variant
+  m->fuse_variant = job->ft.one_round ? 2 : 0;
+  for (int q = 0; q < n_src; ++q) m->fuse_variant |= src[q].topk ? 1 : 0;
+  if (m->graph && m->graph_variant != m->fuse_variant) {  // the graph launches another kernel variant
     cudaGraphExecDestroy(m->graph);
     m->graph = nullptr;
   }
@@ -769,7 +771,7 @@ static mem_status run_points(Map* m, int nm, const int64_t* offsets, int64_t n, 
       e = cudaGraphInstantiate(&m->graph, gph, 0);
       cudaGraphDestroy(gph);
       if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
-      m->graph_topk = m->fuse_topk;
+      m->graph_variant = m->fuse_variant;
     }
     CK(cudaGraphLaunch(m->graph, st), "graph launch");
     return MEM_OK;
@@ -954,8 +956,8 @@ extern "C" mem_status mem_get_origin(const mem_map* mm, int32_t map_index, doubl
   return MEM_OK;
 }
 
-// Autotuner of the point path's schedule: every candidate (radix digit width x
-// persistent-grid size) runs the given batched call `reps` times from the same
+// Autotuner of the point path's schedule: every candidate (fuse kernel x radix
+// digit width x persistent-grid size) runs the given batched call `reps` times from the same
 // saved map state; the fastest is kept and the state is restored.
 extern "C" mem_status mem_autotune_batch(mem_map* mm, const int64_t* offsets, const float* xyz,
                                          int32_t n_sources, const mem_source* sources,
@@ -1002,13 +1004,15 @@ extern "C" mem_status mem_autotune_batch(mem_map* mm, const int64_t* offsets, co
   mem_status s = MEM_OK;
   cudaError_t ce = copy_all(true);
   const int bits_opts[3] = {8, 9, 10}, bps_opts[3] = {2, 4, 8};
-  for (int bi = 0; bi < 3 && ce == cudaSuccess && s == MEM_OK; ++bi) {
+  for (int ki = 0; ki < 6 && ce == cudaSuccess && s == MEM_OK; ++ki) {
+    const int bi = ki % 3, fk = ki / 3;  // both fuse kernels (they differ only where the columns fit one round)
     const int passes = (m->key_bits + bits_opts[bi] - 1) / bits_opts[bi];
     if (passes > 4) continue;
     for (int pi = 0; pi < 3 && ce == cudaSuccess && s == MEM_OK; ++pi) {
       cudaStreamSynchronize(st);
       m->tune.radix_bits = bits_opts[bi];
       m->tune.blocks_per_sm = bps_opts[pi];
+      m->tune.fuse_kernel = fk;
       m->passes = passes;
       if (m->graph) {
         cudaGraphExecDestroy(m->graph);

@@ -13,6 +13,7 @@ constexpr int kJobSlots = 8;
 struct Tuning {
   int radix_bits = 9;   // digit width of the radix sort (8..10)
   int blocks_per_sm = 4;
+  int fuse_kernel = 0;   // 0: the warp fuse kernel where a call's columns fit one round; 1: the tile kernel
 };
 
 struct Map {
@@ -23,8 +24,10 @@ struct Map {
   int passes = 1;
   int key_bits = 1;
   uint32_t call_id = 0;  // point-path calls so far (the clean-up's per-cell stamps)
-  int fuse_topk = 0;      // the current point-path call has a top-k source (fuse kernel variant)
-  int graph_topk = -1;    // the variant the captured graph launches
+  // fuse kernel variant of the current point-path call: bit 0 a source has top-k rows,
+  // bit 1 its columns fit one round (the warp kernel runs instead of the tile kernel)
+  int fuse_variant = 0;
+  int graph_variant = -1;  // the variant the captured graph launches
   int n_sm = 148;
   int device = 0;
   std::vector<double> origin;  // [n_maps][2] world xy of each map centre

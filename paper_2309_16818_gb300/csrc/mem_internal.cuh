@@ -363,6 +363,7 @@ __device__ __forceinline__ void st_relaxed(u32* p, u32 v) {
   asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+
 }  // namespace memk
 
 // host-side launchers (defined in the .cu files)

@@ -171,6 +171,7 @@ extern "C" mem_status mem_fuse_pointcloud_noalloc(const mem_map_config* cfg, con
   hj.job.n_src = 0;
   hj.job.acc = memk::kSlotHdr;
   memh::build_fuse_tables(hj.job, memk::kSlotHdr, *cfg);
+  m.fuse_variant = hj.job.ft.one_round ? 2 : 0;
   for (int r = 0; r < 3; ++r)
     for (int k = 0; k < 3; ++k) hj.mc.R[r * 3 + k] = (float)T_map_sensor[r * 4 + k];
   hj.mc.t[0] = (float)(T_map_sensor[3] - origin_xy[0]);

@@ -456,6 +456,7 @@ constexpr int kQ = 32;          // stage columns per round
 constexpr int kQS = kQ + 1;     // row stride of the stage (odd: conflict-free columns)
 constexpr int kSegMax = 32;     // segments of a tile per walk
 constexpr int kStageU = 6;      // staging chunks in flight per thread
+constexpr int kStageV = 5;      // float4 row loads in flight per thread (warp fuse kernel)
 constexpr int kApplyU = 4;      // rule tasks in flight per thread
 constexpr u32 kBitHead = 1u;    // slot bits: the run begins in the tile
 constexpr u32 kBitEnd = 2u;     //            the run ends in the tile
@@ -1217,6 +1218,544 @@ __global__ void __launch_bounds__(kFT, 7) k_fuse_tiles(MapDev md, const PointJob
   }
 }
 
+// The fusion of one run that crosses tile boundaries, by one warp: it begins in
+// tile h (header and first piece in that tile's slot [1]) and ends in tile
+// `last` (its piece in slot [0]); the tiles between are covered entirely (their
+// slots [1]). Lanes take columns: each adds its column over the pieces in tile
+// order and loads the old values of the column's layers together, then stores
+// the new values; lane 0 updates the height and flags.
+__device__ __forceinline__ void cross_run(const MapDev& md, const LayerDev* sL, const SrcDev* ssrc,
+                                          const int (*srlay)[kMaxSrcLayers], const int* snrlay, int n_src,
+                                          int G, int acc, int h, int last, int lane) {
+  const float* head = fz_slot(md, acc, h, 1);
+  const u32 hw = lane < kSlotHdr ? __float_as_uint(__ldcg(head + lane)) : 0u;
+  const int np = last - h + 1;      // pieces
+  const u32 g = __shfl_sync(0xffffffffu, hw, kSlotKey);
+  const u32 fl0 = __shfl_sync(0xffffffffu, hw, kSlotFl);
+  // points of the run over its pieces
+  u32 n = 0;
+  for (int p = lane; p < np; p += 32)
+    n += __float_as_uint(__ldcg(fz_slot(md, acc, h + p, h + p == last ? 0 : 1) + kSlotN));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
+  const float N = (float)n, rN = __frcp_rn(N);
+  float hsum[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int c0 = 0; c0 < G; c0 += 32) {
+    const int gc = c0 + lane;
+    int q = -1, ch = gc;
+    if (gc < G && gc >= 4) col_ident(ssrc, n_src, gc, q, ch);
+    float S = 0.f;
+    float2 m = make_float2(-INFINITY, __int_as_float(0x7fffffff));
+    float old[kApplyU], s02[kApplyU];
+#pragma unroll
+    for (int j = 0; j < kApplyU; ++j) old[j] = s02[j] = 0.f;
+    if (gc < G) {
+      // four pieces' loads in flight, added in tile order
+      for (int p0 = 0; p0 < np; p0 += 4) {
+        float v[4], w[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          v[u] = 0.f;
+          w[u] = __int_as_float(0x7fffffff);
+          if (p0 + u < np) {
+            const float* sl = fz_slot(md, acc, h + p0 + u, h + p0 + u == last ? 0 : 1) + slot_off(gc);
+            v[u] = __ldcg(sl);
+            if (ch == kChArgV) w[u] = __ldcg(sl + 1);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (p0 + u < np) {
+            S += v[u];
+            if (ch == kChArgV) m = cm_comb(m, make_float2(v[u], w[u]));
+          }
+        }
+      }
+      if (q >= 0 && ch >= 0) {
+#pragma unroll
+        for (int j = 0; j < kApplyU; ++j) {
+          if (j < snrlay[q]) {
+            const int l = srlay[q][j];
+            const LayerDev& L = sL[l];
+            if (fl0 & (2u << l)) {
+              if (L.rule != MEM_RULE_LATEST) old[j] = ld_layer(L, (int64_t)g * L.S + ch);
+              if (L.rule == MEM_RULE_GAUSS) s02[j] = L.gvar[g];
+            }
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float hv = __shfl_sync(0xffffffffu, S, k);
+      if (c0 == 0) hsum[k] = hv;
+    }
+    if (q >= 0 && ch >= 0) {
+#pragma unroll
+      for (int j = 0; j < kApplyU; ++j) {
+        if (j < snrlay[q]) {
+          const int l = srlay[q][j];
+          const LayerDev& L = sL[l];
+          const bool obs = fl0 & (2u << l);
+          st_layer(L, (int64_t)g * L.S + ch, rule_value(L, old[j], S, rule_coef(L, N, rN, obs, s02[j])));
+        }
+      }
+      for (int j = kApplyU; j < snrlay[q]; ++j) {  // more layers than kept in flight
+        const int l = srlay[q][j];
+        const LayerDev& L = sL[l];
+        const bool obs = fl0 & (2u << l);
+        const float s2 = (L.rule == MEM_RULE_GAUSS && obs) ? L.gvar[g] : 0.f;
+        apply_rule(L, (int64_t)g * L.S + ch, S, rule_coef(L, N, rN, obs, s2));
+      }
+    }
+    if (q >= 0 && ch == kChArgV) write_classmax(sL, ssrc[q], g, m.x, m.x == -INFINITY ? -1 : __float_as_int(m.y));
+  }
+  const float h0 = __uint_as_float(__shfl_sync(0xffffffffu, hw, kSlotH0));
+  const float v0 = __uint_as_float(__shfl_sync(0xffffffffu, hw, kSlotV0));
+  const u32 nacc0 = __shfl_sync(0xffffffffu, hw, kSlotNacc), nrej0 = __shfl_sync(0xffffffffu, hw, kSlotNrej);
+  __syncwarp();  // every rule read its Gaussian prior variance
+  if (lane == 0) {
+    u32 fl = fl0;
+    height_update(md, g, fl, h0, v0, hsum[0], hsum[1], (u32)hsum[2], (u32)hsum[3], nacc0, nrej0);
+    for (int q = 0; q < n_src; ++q) {
+      write_gauss_var(sL, ssrc[q], g, fl0, N, rN);
+      for (int b = 0; b < ssrc[q].n_layers; ++b) fl |= 2u << ssrc[q].layers[b];
+    }
+    md.flags[g] = fl;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 4b. the same fusion for calls whose columns fit one round (at most kQ), with
+//     the per-cell sums taken in registers. A warp holds 32 consecutive points
+//     of the tile, one per lane: each lane stages its point's channels in its
+//     own shared-memory row and adds the height sums after the gate; then every
+//     column is summed over the pieces of runs in the warp by a segmented
+//     inclusive scan of shuffles (the piece's sum lands on its last lane; an
+//     arg-max pair takes the segmented maximum instead). The lane where a run
+//     ends adds the pieces of the earlier warps of the tile that the run covers
+//     (in warp order) and fuses the run itself: every layer's rule over its
+//     cell's rows, class max, Kalman height update, Gaussian variances, flags.
+//     Runs that cross the tile's boundaries leave their sums and header in the
+//     tile's two slots exactly as k_fuse_tiles does, for k_fuse_cross.
+
+struct WarpSmem {
+  float stage[kFT * kQS];  // one row per point of the tile
+  SrcDev src[kMaxSources];
+  LayerDev L[kMaxLayers];
+  ChunkDesc ck[kQ];
+  MapCall mc0;
+  int rlay[kMaxSources][kMaxSrcLayers];  // per source: its layers other than class max
+  int nrlay[kMaxSources];
+  int qc0[kMaxSources], qch0[kMaxSources], qn[kMaxSources];
+  int pair_col[kMaxSources];
+  int n_ck, n_pair;
+  u32 whd[kFT / 32];  // per warp: the lanes where a run begins
+};
+
+// One rule layer over the channels of a run, by the lane that fuses it: old
+// values (and the Gaussian prior variance) first, kRuleU vectors in flight.
+template <int RULE, int DT, int W>
+__device__ __forceinline__ void lane_rule_t(const LayerDev& L, int l, const float* S, int ch0, int nch, u32 g,
+                                            u32 fl, float N, float rN) {
+  constexpr int kRuleU = 5;
+  const bool obs = (fl & (2u << l)) != 0;
+  const float s02 = (RULE == MEM_RULE_GAUSS && obs) ? L.gvar[g] : 0.f;
+  const RuleCoef co = rule_coef(L, N, rN, obs, s02);
+  const int64_t base = (int64_t)g * L.S + ch0;
+  for (int k0 = 0; k0 < nch; k0 += kRuleU * W) {
+    float old[kRuleU][W];
+#pragma unroll
+    for (int u = 0; u < kRuleU; ++u) {
+      const int k = k0 + u * W;
+#pragma unroll
+      for (int w = 0; w < W; ++w) old[u][w] = 0.f;
+      if (RULE != MEM_RULE_LATEST && obs && k < nch) {
+        if (W == 4) ld4t<DT>(L.data, base + k, old[u]);
+        else old[u][0] = ld1t<DT>(L.data, base + k);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kRuleU; ++u) {
+      const int k = k0 + u * W;
+      if (k < nch) {
+        float nv[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) nv[w] = rule_value_t<RULE>(L, old[u][w], S[k + w], co);
+        if (W == 4) st4t<DT>(L.data, base + k, nv);
+        else st1t<DT>(L.data, base + k, nv[0]);
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void lane_rule(const LayerDev& L, int l, const float* S, int ch0, int nch, u32 g, u32 fl,
+                                          float N, float rN) {
+  const bool v4 = (L.S & 3) == 0 && (ch0 & 3) == 0 && (nch & 3) == 0;
+#define MEM_LR(R, D)                                                \
+  case R * 4 + D:                                                   \
+    if (v4) lane_rule_t<R, D, 4>(L, l, S, ch0, nch, g, fl, N, rN);  \
+    else lane_rule_t<R, D, 1>(L, l, S, ch0, nch, g, fl, N, rN);     \
+    break;
+  switch (L.rule * 4 + L.dtype) {
+    MEM_LR(MEM_RULE_LATEST, MEM_F32) MEM_LR(MEM_RULE_LATEST, MEM_BF16) MEM_LR(MEM_RULE_LATEST, MEM_F16)
+    MEM_LR(MEM_RULE_EXPAVG, MEM_F32) MEM_LR(MEM_RULE_EXPAVG, MEM_BF16) MEM_LR(MEM_RULE_EXPAVG, MEM_F16)
+    MEM_LR(MEM_RULE_GAUSS, MEM_F32) MEM_LR(MEM_RULE_GAUSS, MEM_BF16) MEM_LR(MEM_RULE_GAUSS, MEM_F16)
+    MEM_LR(MEM_RULE_DIRICHLET, MEM_F32)
+    default: break;
+  }
+#undef MEM_LR
+}
+
+// four (one) source values of any storage type, from their bits
+__device__ __forceinline__ float4 ld4_any(const void* base, int dtype, int64_t off) {
+  if (dtype == MEM_F32) return __ldg(reinterpret_cast<const float4*>((const float*)base + off));
+  if (dtype == MEM_U8) {
+    const u32 b = __ldg(reinterpret_cast<const u32*>((const unsigned char*)base + off));
+    return make_float4((float)(b & 0xffu), (float)((b >> 8) & 0xffu), (float)((b >> 16) & 0xffu), (float)(b >> 24));
+  }
+  const uint2 q = __ldg(reinterpret_cast<const uint2*>((const uint16_t*)base + off));
+  if (dtype == MEM_BF16)
+    return make_float4(__uint_as_float(q.x << 16), __uint_as_float(q.x & 0xffff0000u), __uint_as_float(q.y << 16),
+                       __uint_as_float(q.y & 0xffff0000u));
+  return make_float4(__half2float(__ushort_as_half((unsigned short)(q.x & 0xffffu))),
+                     __half2float(__ushort_as_half((unsigned short)(q.x >> 16))),
+                     __half2float(__ushort_as_half((unsigned short)(q.y & 0xffffu))),
+                     __half2float(__ushort_as_half((unsigned short)(q.y >> 16))));
+}
+__device__ __forceinline__ float ld1_any(const void* base, int dtype, int64_t off) {
+  if (dtype == MEM_F32) return __ldg((const float*)base + off);
+  if (dtype == MEM_U8) return (float)__ldg((const unsigned char*)base + off);
+  const unsigned short b = __ldg((const unsigned short*)base + off);
+  return dtype == MEM_BF16 ? __uint_as_float((u32)b << 16) : __half2float(__ushort_as_half(b));
+}
+
+// One source's channels of a point into its stage row (columns col0 .. col0 +
+// C - 1), then, for a source bound to a class-max layer, the point's largest
+// channel value and its channel (the smaller channel on ties) in the next two
+// columns. Rows of C % 4 == 0 channels of 16-byte aligned data are read four
+// channels at a time.
+__device__ __forceinline__ void stage_src(float* srow, const void* data, int dtype, int64_t id, int C, int col0,
+                                          bool vec, bool cm) {
+  float pb = -INFINITY;
+  int pi = 0x7fffffff;
+  const int64_t base = id * C;
+  if (vec && (C & 3) == 0) {
+    for (int k0 = 0; k0 < C; k0 += 4 * kStageV) {
+      float4 v[kStageV];
+#pragma unroll
+      for (int u = 0; u < kStageV; ++u)
+        if (k0 + 4 * u < C) v[u] = ld4_any(data, dtype, base + k0 + 4 * u);
+#pragma unroll
+      for (int u = 0; u < kStageV; ++u)
+        if (k0 + 4 * u < C)
+#pragma unroll
+          for (int w = 0; w < 4; ++w) {
+            const float e = w == 0 ? v[u].x : w == 1 ? v[u].y : w == 2 ? v[u].z : v[u].w;
+            srow[col0 + k0 + 4 * u + w] = e;
+            if (cm && e > pb) {
+              pb = e;
+              pi = k0 + 4 * u + w;
+            }
+          }
+    }
+  } else {
+    for (int k0 = 0; k0 < C; k0 += 8) {
+      float v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (k0 + u < C) v[u] = ld1_any(data, dtype, base + k0 + u);
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (k0 + u < C) {
+          srow[col0 + k0 + u] = v[u];
+          if (cm && v[u] > pb) {
+            pb = v[u];
+            pi = k0 + u;
+          }
+        }
+    }
+  }
+  if (cm) {
+    srow[col0 + C] = pb;
+    srow[col0 + C + 1] = __int_as_float(pi);
+  }
+}
+
+// The chunks of the top-k sources (rows of (class id, probability) pairs
+// expanded into channels), with their arg-max.
+__device__ __noinline__ void stage_topk_chunks(const ChunkDesc* ck, int nck, const SrcDev* src, float* srow,
+                                               int64_t id) {
+  float pb = -INFINITY;
+  int pi = 0x7fffffff;
+  for (int k = 0; k < nck; ++k) {
+    const ChunkDesc& d = ck[k];
+    if (!src[d.src].topk) continue;
+    float v[4];
+    ld_chunk<true>(d, id, v);
+    for (int w = 0; w < d.n; ++w) {
+      srow[d.col + w] = v[w];
+      if (d.am >= 0 && v[w] > pb) {
+        pb = v[w];
+        pi = d.ch0 + w;
+      }
+    }
+    if (d.am >= 0 && (d.am >> 30)) {
+      srow[d.am & 0xffff] = pb;
+      srow[(d.am & 0xffff) + 1] = __int_as_float(pi);
+      pb = -INFINITY;
+      pi = 0x7fffffff;
+    }
+  }
+}
+
+template <bool TOPK, bool RAY>
+__global__ void __launch_bounds__(kFT, 6) k_fuse_warps(MapDev md, const PointJob* __restrict__ job, int sorted1) {
+  extern __shared__ __align__(16) unsigned char fw_raw[];
+  WarpSmem& s = *reinterpret_cast<WarpSmem*>(fw_raw);
+  if (*(volatile int*)md.err) return;  // a device error is pending: the point path does nothing
+  const u32* __restrict__ sk = sorted1 ? md.keys1 : md.keys0;
+  const u32* __restrict__ sv = sorted1 ? md.vals1 : md.vals0;
+  const int64_t n_kept = *(volatile u32*)&md.counters[6];
+  const int n_tiles = (int)((n_kept + kFT - 1) / kFT);
+  const int n_src = job->n_src;
+  const int acc = job->acc;
+  const FuseTables* __restrict__ ft = &job->ft;
+  const int G = ft->ncol;  // columns of the call (at most kQ)
+  const bool any_gauss = ft->any_gauss;
+  const float* __restrict__ xyz = job->xyz;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const u64 call_hi = RAY ? (u64)job->call_id << 32 : 0ull;
+  // the call's tables (built on the host) into shared memory
+  if (t < n_src) s.src[t] = job->src[t];
+  if (t < md.n_layers) s.L[t] = md.L[t];
+  if (t < kQ) s.ck[t] = ft->ck[t];
+  if (t < kMaxSources) {
+    s.nrlay[t] = ft->nrlay[t];
+    for (int b = 0; b < kMaxSrcLayers; ++b) s.rlay[t][b] = ft->rlay[t][b];
+    s.qc0[t] = ft->qc0[t];
+    s.qch0[t] = ft->qch0[t];
+    s.qn[t] = ft->qn[t];
+    s.pair_col[t] = ft->pair_col[t];
+  }
+  if (t == 0) {
+    s.mc0 = job->maps[0];
+    s.n_ck = ft->n_ck;
+    s.n_pair = ft->n_pair;
+  }
+  // columns of the arg-max pairs (value, channel): maxima, not sums
+  u32 am_val = 0;
+  for (int k = 0; k < ft->n_pair; ++k) am_val |= 1u << ft->pair_col[k];
+  const u32 am_any = am_val | (am_val << 1);
+  const u32 le = 0xffffffffu >> (31 - lane);  // lanes up to this one
+  u32 heads = 0;  // runs that begin at this thread's points
+  float* srow = s.stage + t * kQS;
+  for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    __syncthreads();  // tables in place; the previous tile is done with the stage
+    const int64_t p0 = (int64_t)tile * kFT;
+    const int np = (int)min((int64_t)kFT, n_kept - p0);
+    const int64_t p = p0 + t;
+    const bool on = t < np;
+    // A. key, neighbours' keys, runs and pieces
+    u32 key = 0xfffffffeu, kprev = 0xfffffffeu, knext = 0xfffffffeu, id = 0;
+    if (on) {
+      key = sk[p];
+      id = sv[p];
+      if (p > 0) kprev = sk[p - 1];
+      if (p + 1 < n_kept) knext = sk[p + 1];
+    }
+    const bool hd = on && key != kprev;  // a run begins here
+    const bool ed = on && key != knext;  // a run ends here
+    const bool tl = t == np - 1;         // the tile's last point
+    const u32 hb = __ballot_sync(0xffffffffu, hd);
+    if (lane == 0) s.whd[warp] = hb;
+    heads += hd ? 1u : 0u;
+    const int hl = 31 - __clz((hb | 1u) & le);  // first lane of this lane's piece (run within the warp)
+    // pre-call state of the cell (the gate's), coordinates
+    u32 fl = 0;
+    float h0 = 0.f, v0 = 0.f, xs = 0.f, ys = 0.f, zs = 0.f;
+    if (on) {
+      fl = md.flags[key];
+      h0 = md.h[key];
+      v0 = md.var[key];
+      xs = __ldg(xyz + 3 * (int64_t)id);
+      ys = __ldg(xyz + 3 * (int64_t)id + 1);
+      zs = __ldg(xyz + 3 * (int64_t)id + 2);
+    }
+    if (ed) {  // rule layers' rows of a cell this lane may fuse, into L2
+      for (int q = 0; q < n_src; ++q)
+        for (int j = 0; j < s.nrlay[q]; ++j) {
+          const LayerDev& L = s.L[s.rlay[q][j]];
+          if (L.rule == MEM_RULE_LATEST) continue;
+          const int bytes = L.S * (L.dtype == MEM_F32 ? 4 : 2);
+          const char* row = (const char*)L.data + (int64_t)key * bytes;
+          for (int o = 0; o < bytes; o += 128) prefetch_l2(row + o);
+          prefetch_l2(row + bytes - 1);
+        }
+    }
+    // B. the point's channels into its row, with the arg-max of a class-max
+    //    source on the way (top-k sources by the chunk table)
+    if (on) {
+      for (int q = 0; q < n_src; ++q) {
+        const SrcDev& S = s.src[q];
+        if (TOPK && S.topk) continue;
+        stage_src(srow, S.data, S.dtype, id, S.C, s.qc0[q], S.vec_ok, S.has_classmax);
+      }
+      if (TOPK) stage_topk_chunks(s.ck, s.n_ck, s.src, srow, id);
+    }
+    // C. outlier gate against the pre-call state: the point's height sums
+    u64 zk = 0;  // ray-cast clean-up: (call id, lowest z) key of an accepted point
+    if (on) {
+      const MapCall* mc = md.n_maps > 1 ? job->maps + key / md.W2 : &s.mc0;
+      float z, vm;
+      eval_zvm(md, *mc, xs, ys, zs, z, vm);
+      const bool rej = (fl & kFlagValid) && gate_reject(z, h0, v0, vm, md.lam2);
+      const float w = __frcp_rn(vm);
+      srow[0] = rej ? 0.f : w;
+      srow[1] = rej ? 0.f : z * w;
+      srow[2] = rej ? 0.f : 1.f;
+      srow[3] = rej ? 1.f : 0.f;
+      if (RAY && !rej) zk = call_hi | (u64)(~ordered_bits(__float_as_uint(z)));
+    }
+    // D. sums over the pieces of runs in the warp: lane c walks column c down
+    //    the warp's rows in point order and leaves each piece's sum in the
+    //    piece's last row; the arg-max pairs take a segmented maximum by
+    //    shuffles (the piece's last lane ends with the piece's pair)
+    __syncwarp();  // every lane's row is staged
+    const u32 pm = __ballot_sync(0xffffffffu, on && (ed || lane == 31 || tl));  // last lanes of pieces
+    {
+      const bool keep = lane < G && !((am_any >> lane) & 1u);
+      float* col = s.stage + warp * 32 * kQS + lane;
+      const int nv = min(32, np - warp * 32);  // points of this warp (warp-uniform)
+      float a = 0.f;
+      for (int i0 = 0; i0 < nv; i0 += 8) {
+        float x[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) x[u] = col[(i0 + u) * kQS];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          if (i0 + u < nv) {
+            a += x[u];
+            if ((pm >> (i0 + u)) & 1u) {
+              if (keep) col[(i0 + u) * kQS] = a;
+              a = 0.f;
+            }
+          }
+        }
+      }
+    }
+    if (s.n_pair) {
+      bool take[5];
+#pragma unroll
+      for (int k = 0; k < 5; ++k) take[k] = lane - (1 << k) >= hl;
+      for (int k = 0; k < s.n_pair; ++k) {
+        const int c = s.pair_col[k];
+        float2 m = make_float2(srow[c], srow[c + 1]);
+#pragma unroll
+        for (int b = 0; b < 5; ++b) {
+          const float ov = __shfl_up_sync(0xffffffffu, m.x, 1 << b);
+          const float oi = __shfl_up_sync(0xffffffffu, m.y, 1 << b);
+          if (take[b]) m = cm_comb(make_float2(ov, oi), m);
+        }
+        srow[c] = m.x;
+        srow[c + 1] = m.y;
+      }
+    }
+    if (RAY) {  // the lowest accepted z of every cell: segmented maximum of the keys, one atomic per piece
+#pragma unroll
+      for (int k = 0; k < 5; ++k) {
+        const u64 o = __shfl_up_sync(0xffffffffu, zk, 1 << k);
+        if (lane - (1 << k) >= hl && o > zk) zk = o;
+      }
+      if (on && zk != 0 && ((pm >> lane) & 1u)) atomicMax((unsigned long long*)(md.zacc + key), (unsigned long long)zk);
+    }
+    if (t == 0) {  // both slots unused unless a piece below writes one
+      fz_slot(md, acc, tile, 0)[kSlotBits] = 0.f;
+      fz_slot(md, acc, tile, 1)[kSlotBits] = 0.f;
+    }
+    __syncthreads();  // every warp's last row (the piece continuing into the next warp) is complete
+    // E. the lane where a run ends, or where the tile ends inside a run: the
+    //    run's sums over the tile, then the run is fused here or its piece
+    //    goes to a slot
+    if (on && (ed || tl)) {
+      int ht = -1;  // tile index of the run's first point (-1: the run began in an earlier tile)
+      int w1 = warp;
+      if ((hb >> hl) & 1u) {
+        ht = warp * 32 + hl;
+      } else {
+        w1 = 0;
+        for (int w = warp - 1; w >= 0; --w) {
+          const u32 b = s.whd[w];
+          if (b) {
+            ht = w * 32 + 31 - __clz(b);
+            w1 = w;
+            break;
+          }
+        }
+      }
+      if (w1 < warp) {  // the pieces of earlier warps, in warp order, then this lane's piece
+        for (int c = 0; c < G; ++c) {
+          if ((am_val >> c) & 1u) {
+            float2 m = make_float2(s.stage[(w1 * 32 + 31) * kQS + c], s.stage[(w1 * 32 + 31) * kQS + c + 1]);
+            for (int w = w1 + 1; w < warp; ++w)
+              m = cm_comb(m, make_float2(s.stage[(w * 32 + 31) * kQS + c], s.stage[(w * 32 + 31) * kQS + c + 1]));
+            m = cm_comb(m, make_float2(srow[c], srow[c + 1]));
+            srow[c] = m.x;
+            srow[c + 1] = m.y;
+            ++c;
+          } else {
+            float a = s.stage[(w1 * 32 + 31) * kQS + c];
+            for (int w = w1 + 1; w < warp; ++w) a += s.stage[(w * 32 + 31) * kQS + c];
+            srow[c] = a + srow[c];
+          }
+        }
+      }
+      const u32 nt = (u32)(t - max(ht, 0) + 1);  // points of the run in the tile
+      const u32 g = key;
+      const u32 na0 = md.n_acc[g], nr0 = md.n_rej[g];
+      if (ht >= 0 && ed) {
+        // the whole run lies in the tile: every layer's rule, class max, height, flags
+        const float N = (float)nt, rN = __frcp_rn(N);
+        for (int q = 0; q < n_src; ++q)
+          if (s.qn[q] > 0)
+            for (int j = 0; j < s.nrlay[q]; ++j) {
+              const int l = s.rlay[q][j];
+              lane_rule(s.L[l], l, srow + s.qc0[q], s.qch0[q], s.qn[q], g, fl, N, rN);
+            }
+        for (int q = 0; q < n_src; ++q)
+          if (s.src[q].has_classmax) {
+            const int av = s.qc0[q] + s.src[q].C;  // arg-max value column
+            const float best = srow[av];
+            write_classmax(s.L, s.src[q], g, best, best == -INFINITY ? -1 : __float_as_int(srow[av + 1]));
+          }
+        u32 f = fl;
+        height_update(md, g, f, h0, v0, srow[0], srow[1], (u32)srow[2], (u32)srow[3], na0, nr0);
+        for (int q = 0; q < n_src; ++q) {
+          if (any_gauss) write_gauss_var(s.L, s.src[q], g, f, N, rN);
+          for (int b = 0; b < s.src[q].n_layers; ++b) f |= 2u << s.src[q].layers[b];
+        }
+        md.flags[g] = f;
+      } else {
+        // [0]: a run begun in an earlier tile that ends here; [1]: a run that continues past the tile
+        float* hdr = fz_slot(md, acc, tile, ed ? 0 : 1);
+        const u32 bits = kBitUsed | (ht >= 0 ? kBitHead : 0u) | (ed ? kBitEnd : 0u);
+        hdr[kSlotKey] = __uint_as_float(g);
+        hdr[kSlotN] = __uint_as_float(nt);
+        hdr[kSlotBits] = __uint_as_float(bits);
+        hdr[kSlotFl] = __uint_as_float(fl);
+        hdr[kSlotH0] = h0;
+        hdr[kSlotV0] = v0;
+        hdr[kSlotNacc] = __uint_as_float(na0);
+        hdr[kSlotNrej] = __uint_as_float(nr0);
+        for (int c = 0; c < G; ++c) hdr[slot_off(c)] = srow[c];
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) heads += __shfl_xor_sync(0xffffffffu, heads, o);
+  if (lane == 0 && heads) atomicAdd(&md.counters[5], heads);
+}
+
 // ---------------------------------------------------------------------------
 
 // One warp per run that crosses tile boundaries, started from the tile where
@@ -1265,100 +1804,7 @@ __global__ void __launch_bounds__(128) k_fuse_cross(MapDev md, const PointJob* _
       if (em) last = t0 + __ffs(em) - 1;
     }
     if (last < 0) last = n_tiles - 1;  // not reached for a consistent slot table
-    const int np = last - h + 1;      // pieces
-    const u32 g = __shfl_sync(0xffffffffu, hw, kSlotKey);
-    const u32 fl0 = __shfl_sync(0xffffffffu, hw, kSlotFl);
-    // points of the run over its pieces
-    u32 n = 0;
-    for (int p = lane; p < np; p += 32)
-      n += __float_as_uint(__ldcg(fz_slot(md, acc, h + p, h + p == last ? 0 : 1) + kSlotN));
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
-    const float N = (float)n, rN = __frcp_rn(N);
-    float hsum[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int c0 = 0; c0 < G; c0 += 32) {
-      const int gc = c0 + lane;
-      int q = -1, ch = gc;
-      if (gc < G && gc >= 4) col_ident(ssrc, n_src, gc, q, ch);
-      float S = 0.f;
-      float2 m = make_float2(-INFINITY, __int_as_float(0x7fffffff));
-      float old[kApplyU], s02[kApplyU];
-#pragma unroll
-      for (int j = 0; j < kApplyU; ++j) old[j] = s02[j] = 0.f;
-      if (gc < G) {
-        // four pieces' loads in flight, added in tile order
-        for (int p0 = 0; p0 < np; p0 += 4) {
-          float v[4], w[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            v[u] = 0.f;
-            w[u] = __int_as_float(0x7fffffff);
-            if (p0 + u < np) {
-              const float* sl = fz_slot(md, acc, h + p0 + u, h + p0 + u == last ? 0 : 1) + slot_off(gc);
-              v[u] = __ldcg(sl);
-              if (ch == kChArgV) w[u] = __ldcg(sl + 1);
-            }
-          }
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            if (p0 + u < np) {
-              S += v[u];
-              if (ch == kChArgV) m = cm_comb(m, make_float2(v[u], w[u]));
-            }
-          }
-        }
-        if (q >= 0 && ch >= 0) {
-#pragma unroll
-          for (int j = 0; j < kApplyU; ++j) {
-            if (j < snrlay[q]) {
-              const int l = srlay[q][j];
-              const LayerDev& L = sL[l];
-              if (fl0 & (2u << l)) {
-                if (L.rule != MEM_RULE_LATEST) old[j] = ld_layer(L, (int64_t)g * L.S + ch);
-                if (L.rule == MEM_RULE_GAUSS) s02[j] = L.gvar[g];
-              }
-            }
-          }
-        }
-      }
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const float hv = __shfl_sync(0xffffffffu, S, k);
-        if (c0 == 0) hsum[k] = hv;
-      }
-      if (q >= 0 && ch >= 0) {
-#pragma unroll
-        for (int j = 0; j < kApplyU; ++j) {
-          if (j < snrlay[q]) {
-            const int l = srlay[q][j];
-            const LayerDev& L = sL[l];
-            const bool obs = fl0 & (2u << l);
-            st_layer(L, (int64_t)g * L.S + ch, rule_value(L, old[j], S, rule_coef(L, N, rN, obs, s02[j])));
-          }
-        }
-        for (int j = kApplyU; j < snrlay[q]; ++j) {  // more layers than kept in flight
-          const int l = srlay[q][j];
-          const LayerDev& L = sL[l];
-          const bool obs = fl0 & (2u << l);
-          const float s2 = (L.rule == MEM_RULE_GAUSS && obs) ? L.gvar[g] : 0.f;
-          apply_rule(L, (int64_t)g * L.S + ch, S, rule_coef(L, N, rN, obs, s2));
-        }
-      }
-      if (q >= 0 && ch == kChArgV) write_classmax(sL, ssrc[q], g, m.x, m.x == -INFINITY ? -1 : __float_as_int(m.y));
-    }
-    const float h0 = __uint_as_float(__shfl_sync(0xffffffffu, hw, kSlotH0));
-    const float v0 = __uint_as_float(__shfl_sync(0xffffffffu, hw, kSlotV0));
-    const u32 nacc0 = __shfl_sync(0xffffffffu, hw, kSlotNacc), nrej0 = __shfl_sync(0xffffffffu, hw, kSlotNrej);
-    __syncwarp();  // every rule read its Gaussian prior variance
-    if (lane == 0) {
-      u32 fl = fl0;
-      height_update(md, g, fl, h0, v0, hsum[0], hsum[1], (u32)hsum[2], (u32)hsum[3], nacc0, nrej0);
-      for (int q = 0; q < n_src; ++q) {
-        write_gauss_var(sL, ssrc[q], g, fl0, N, rN);
-        for (int b = 0; b < ssrc[q].n_layers; ++b) fl |= 2u << ssrc[q].layers[b];
-      }
-      md.flags[g] = fl;
-    }
+    cross_run(md, sL, ssrc, srlay, snrlay, n_src, G, acc, h, last, lane);
   }
   if (lane == 0 && crossing) atomicAdd(&md.counters[4], crossing);
 }
@@ -1503,8 +1949,9 @@ using namespace memk;
 // Kernel attributes are per device: the current device's index selects the
 // entry of these tables (set by prepare_kernels with that device current).
 constexpr int kMaxDevices = 128;
-// resident CTAs per SM of the tile fuse kernel (its persistent grid)
+// resident CTAs per SM of the tile and warp fuse kernels (their persistent grids)
 static int g_sums_ctas_per_sm[kMaxDevices] = {};
+static int g_warps_ctas_per_sm[kMaxDevices] = {};
 
 static int current_device() {
   int d = 0;
@@ -1565,14 +2012,27 @@ static cudaError_t launch_rb(Map* m, const PointJob* d_job, cudaStream_t st) {
   }
   {
     ProfScope ps(m, kProfFuseTiles, st);
-    const int cps = g_sums_ctas_per_sm[current_device()];
-    const dim3 grid(sms * (cps > 0 ? cps : 1));
-    if (m->fuse_topk)
-      md.ray_on ? k_fuse_tiles<true, true><<<grid, kFT, sizeof(SumSmem), st>>>(md, d_job, P & 1)
-                : k_fuse_tiles<true, false><<<grid, kFT, sizeof(SumSmem), st>>>(md, d_job, P & 1);
-    else
-      md.ray_on ? k_fuse_tiles<false, true><<<grid, kFT, sizeof(SumSmem), st>>>(md, d_job, P & 1)
-                : k_fuse_tiles<false, false><<<grid, kFT, sizeof(SumSmem), st>>>(md, d_job, P & 1);
+    const bool topk = m->fuse_variant & 1;
+    if ((m->fuse_variant & 2) && m->tune.fuse_kernel == 0) {  // the columns fit one round: warp kernel
+      const int cps = g_warps_ctas_per_sm[current_device()];
+      const dim3 grid(sms * (cps > 0 ? cps : 1));
+      const size_t sm = sizeof(WarpSmem);
+      if (topk)
+        md.ray_on ? k_fuse_warps<true, true><<<grid, kFT, sm, st>>>(md, d_job, P & 1)
+                  : k_fuse_warps<true, false><<<grid, kFT, sm, st>>>(md, d_job, P & 1);
+      else
+        md.ray_on ? k_fuse_warps<false, true><<<grid, kFT, sm, st>>>(md, d_job, P & 1)
+                  : k_fuse_warps<false, false><<<grid, kFT, sm, st>>>(md, d_job, P & 1);
+    } else {
+      const int cps = g_sums_ctas_per_sm[current_device()];
+      const dim3 grid(sms * (cps > 0 ? cps : 1));
+      if (topk)
+        md.ray_on ? k_fuse_tiles<true, true><<<grid, kFT, sizeof(SumSmem), st>>>(md, d_job, P & 1)
+                  : k_fuse_tiles<true, false><<<grid, kFT, sizeof(SumSmem), st>>>(md, d_job, P & 1);
+      else
+        md.ray_on ? k_fuse_tiles<false, true><<<grid, kFT, sizeof(SumSmem), st>>>(md, d_job, P & 1)
+                  : k_fuse_tiles<false, false><<<grid, kFT, sizeof(SumSmem), st>>>(md, d_job, P & 1);
+    }
   }
   {
     ProfScope ps(m, kProfFuseCross, st);
@@ -1597,6 +2057,13 @@ cudaError_t prepare_kernels() {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_sums_ctas_per_sm[dev], k_fuse_tiles<false, false>, kFT,
                                                       sizeof(SumSmem));
   if (g_sums_ctas_per_sm[dev] < 1) g_sums_ctas_per_sm[dev] = 1;
+  for (auto f : {k_fuse_warps<false, false>, k_fuse_warps<false, true>, k_fuse_warps<true, false>,
+                 k_fuse_warps<true, true>})
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(WarpSmem));
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_warps_ctas_per_sm[dev], k_fuse_warps<false, false>, kFT,
+                                                      sizeof(WarpSmem));
+  if (g_warps_ctas_per_sm[dev] < 1) g_warps_ctas_per_sm[dev] = 1;
   if (e == cudaSuccess) e = set_attrs<8>();
   if (e == cudaSuccess) e = set_attrs<9>();
   if (e == cudaSuccess) e = set_attrs<10>();

@@ -93,7 +93,7 @@ def lib():
             "mem_fuse_image": [P, I32, I32, I32, I32, P, P, P, P, P, P],
             "mem_get_layer": [P, I32, I32, I32, P, P], "mem_set_layer": [P, I32, I32, I32, P, P],
             "mem_get_origin": [P, I32, P], "mem_check": [P, P], "mem_last_error": [],
-            "mem_set_tuning": [P, I32, I32], "mem_get_tuning": [P, P],
+            "mem_set_tuning": [P, I32, I32, I32], "mem_get_tuning": [P, P],
             "mem_set_profiling": [P, I32], "mem_get_profile": [P, P, P], "mem_get_stats": [P, P, P],
             "mem_fuse_pointcloud_noalloc": [P, P, I64, P, P, P, P, P, P, P, P],
             "mem_autotune_batch": [P, P, P, I32, P, P, I32, P, P, P],
@@ -365,13 +365,16 @@ class Map:
         """Tests only: FAULT_SORT_WAIT makes the sort's bounded waits run out; FAULT_NONE clears."""
         _ck(lib().mem_inject_fault(self._h, kind))
 
-    def set_tuning(self, radix_bits, blocks_per_sm):
-        _ck(lib().mem_set_tuning(self._h, radix_bits, blocks_per_sm))
+    def set_tuning(self, radix_bits, blocks_per_sm, fuse_kernel=0):
+        """fuse_kernel 0: per-cell sums in registers where the call's columns fit one round;
+        1: the shared-memory tile kernel always."""
+        _ck(lib().mem_set_tuning(self._h, radix_bits, blocks_per_sm, fuse_kernel))
 
     def get_tuning(self):
         out = np.zeros(4, np.int32)
         _ck(lib().mem_get_tuning(self._h, out.ctypes.data))
-        return dict(radix_bits=int(out[0]), blocks_per_sm=int(out[1]), passes=int(out[2]))
+        return dict(radix_bits=int(out[0]), blocks_per_sm=int(out[1]), passes=int(out[2]),
+                    fuse_kernel=int(out[3]))
 
     def autotune_batch(self, offsets, xyz, T, sources=(), reps=3, stream=None):
         """Pick the fastest schedule for this batched call; the map state is left unchanged.
@@ -380,8 +383,8 @@ class Map:
         src = self._sources(list(sources), keep)
         off = np.ascontiguousarray(offsets, dtype=np.int64)
         Tb = _pose(T, self.n_maps)
-        ms = np.zeros(16, np.float32)
-        n = C.c_int32(16)
+        ms = np.zeros(32, np.float32)
+        n = C.c_int32(32)
         _ck(lib().mem_autotune_batch(self._h, off.ctypes.data,
                                      C.c_void_p(xyz.data_ptr() if xyz.numel() else 0), len(sources),
                                      src, Tb.ctypes.data, reps, _stream(stream), ms.ctypes.data,

@@ -135,7 +135,7 @@ def test_batched_full_size_equals_per_map_oracle(torch, radix_bits):
     assert int(c["offsets"][-1]) > 10_000_000
     layers = [dict(channels=3, rule=O.LATEST), dict(channels=16, rule=O.GAUSS, dtype=O.BF16)]
     g, _ = make_pair(c["W"], c["res"], layers, n_maps=B, max_points=int(c["offsets"][-1]) + 4096)
-    g.set_tuning(radix_bits, 4)
+    g.set_tuning(radix_bits, 4, 1 if radix_bits == 8 else 0)  # both fuse kernels at full size
     assert g.get_tuning()["passes"] == (4 if radix_bits == 8 else 3)
     g.fuse_pointcloud_batch(c["offsets"], torch.from_numpy(xyz).cuda(), T, _batch_sources(torch, rgb, feat))
     g.check()

@@ -35,13 +35,15 @@ def test_config1_height_and_colour(torch):
     compare_states(gs, o, what="config 1")
 
 
-@pytest.mark.parametrize("radix_bits,bps", [(8, 4), (9, 1), (10, 2), (9, 8)])
-def test_multimodal_scan_sequence(torch, radix_bits, bps):
+@pytest.mark.parametrize("radix_bits,bps,fuse_kernel", [(8, 4, 0), (9, 1, 1), (10, 2, 0), (9, 8, 1), (9, 4, 0)])
+def test_multimodal_scan_sequence(torch, radix_bits, bps, fuse_kernel):
     """Several poses of the multi-modal workload (reduced sensors), each step starting both
-    sides from the same (oracle) state: move, then fuse, then compare."""
+    sides from the same (oracle) state: move, then fuse, then compare. Both fuse kernels
+    (register sums, shared-memory column walks) under several sort schedules."""
     c = synth.config2(n_poses=3, scale=0.25)
     g, o = make_pair(c["W"], c["res"], multimodal_layers(), max_points=1 << 16)
-    g.set_tuning(radix_bits, bps)
+    g.set_tuning(radix_bits, bps, fuse_kernel)
+    assert g.get_tuning()["fuse_kernel"] == fuse_kernel
     for k, scan in enumerate(c["scans"]):
         upload_state(g, o)
         xy = c["poses"][k][:2]
@@ -53,6 +55,31 @@ def test_multimodal_scan_sequence(torch, radix_bits, bps):
         g.check()
         compare_states(gpu_state(g), o, what=f"pose {k}")
     assert o.valid.sum() > 2000 and o.n_rej.sum() > 0
+
+
+@pytest.mark.parametrize("order", ["pair_in_round", "pair_after_its_channels"])
+def test_columns_over_several_rounds(torch, order):
+    """More summed columns than one round holds (4 height sums + 3 colour + 24 features +
+    20 classes + the arg-max pair = 53): the tile kernel takes them in rounds. With the
+    features first, the class source's channels begin in the first round and its arg-max pair
+    falls in the second, which recomputes the per-point arg-max there."""
+    c = synth.config2(n_poses=2, scale=0.25)
+    layers = [dict(channels=3, rule=O.LATEST), dict(channels=20, rule=O.DIRICHLET, alpha0=1.0),
+              dict(channels=20, rule=O.CLASSMAX), dict(channels=24, rule=O.GAUSS, var_meas=0.3),
+              dict(channels=24, rule=O.EXPAVG, w=0.2)]
+    g, o = make_pair(c["W"], c["res"], layers, max_points=1 << 16)
+    rng = np.random.default_rng(11)
+    for k, scan in enumerate(c["scans"]):
+        feat = rng.normal(0.0, 1.0, (scan.n, 24)).astype(np.float32)
+        src_np = [(scan.rgb, [0]), (scan.probs, [1, 2]), (feat, [3, 4])]
+        if order == "pair_after_its_channels":
+            src_np = [src_np[0], src_np[2], src_np[1]]
+        src_gpu = [(torch.from_numpy(np.ascontiguousarray(a)).cuda(), ls) for a, ls in src_np]
+        upload_state(g, o)
+        o.fuse_points(scan.xyz, scan.T, src_np)
+        g.fuse_pointcloud(cuda_xyz(scan), scan.T, src_gpu)
+        g.check()
+        compare_states(gpu_state(g), o, what=f"{order} pose {k}")
 
 
 def test_full_size_multimodal_pose(torch):
@@ -246,7 +273,8 @@ def test_graph_replay_on_a_side_stream_equals_eager(torch):
             assert np.array_equal(a.view(np.uint8), b.view(np.uint8)), (k, layer)
 
 
-def test_run_to_run_identical_with_moves(torch):
+@pytest.mark.parametrize("fuse_kernel", [0, 1])
+def test_run_to_run_identical_with_moves(torch, fuse_kernel):
     """Every sum is taken in a fixed order, so the same pose sequence (with map moves, which
     wrap the ring-buffer keys) on fresh maps must give bit-identical layers, repeatedly."""
     from paper_2309_16818_gb300 import mem as M
@@ -257,8 +285,7 @@ def test_run_to_run_identical_with_moves(torch):
     ref = None
     for trial in range(4):
         g = M.Map(c["W"], c["res"], layers, max_points=1 << 20)
-        if trial % 2:
-            g.set_tuning(9, 8)
+        g.set_tuning(9, 8 if trial % 2 else 4, fuse_kernel)
         out = []
         for k, s in enumerate(c["scans"]):
             g.move(c["poses"][k][:2])
