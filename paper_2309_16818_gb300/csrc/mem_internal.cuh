@@ -18,8 +18,8 @@ constexpr int kMaxSrcLayers = MEM_MAX_SOURCE_LAYERS;
 constexpr u32 kFlagValid = 1u;               // bit 0: height valid
 constexpr u32 kSpinLimit = 1u << 22;         // bounded waits (x ~100 ns each)
 constexpr int kDevErrTimeout = 1;
-constexpr int kSortThreads = 256;            // threads of a radix-sort CTA
-constexpr int kSortItems = 12;               // keys per thread
+constexpr int kSortThreads = 512;            // threads of a radix-sort CTA (two per SM)
+constexpr int kSortItems = 6;                // keys per thread
 constexpr int kSortTile = kSortThreads * kSortItems;  // keys per radix tile (look-back unit)
 constexpr int kFuseTile = 128;               // sorted points per tile of the fuse kernels
 constexpr int kSlotHdr = 16;                 // words of a fuse slot before its channel sums

@@ -221,11 +221,11 @@ __global__ void __launch_bounds__(256) k_drift_apply(MapDev md) {
 // 3. one stable radix pass (onesweep: tiles taken in order from a counter,
 //    global digit prefixes by decoupled look-back with bounded waits)
 template <int RB>
-__global__ void __launch_bounds__(kSortThreads) k_onesweep(MapDev md, const PointJob* __restrict__ job,
+__global__ void __launch_bounds__(kSortThreads, 2) k_onesweep(MapDev md, const PointJob* __restrict__ job,
                                                            int pass) {
   constexpr int RADIX = 1 << RB;
   constexpr int WARPS = kSortThreads / 32;
-  constexpr int RPT = RADIX / kSortThreads;
+  constexpr int RPT = (RADIX + kSortThreads - 1) / kSortThreads;  // digits per thread (threads past RADIX: none)
   extern __shared__ __align__(16) u32 sm[];
   u32* whist = sm;                       // [WARPS][RADIX]
   u32* skeys = whist + WARPS * RADIX;    // [kTile]
@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(MapDev md, const Poin
     u32 tsum = 0;
 #pragma unroll
     for (int r = 0; r < RPT; ++r) {
-      loc[r] = md.hist[pass * RADIX + threadIdx.x * RPT + r];
+      loc[r] = threadIdx.x * RPT + r < RADIX ? md.hist[pass * RADIX + threadIdx.x * RPT + r] : 0u;
       tsum += loc[r];
     }
     u32 inc = tsum;
@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(MapDev md, const Poin
     for (int w = 0; w < warp; ++w) run += s_wsum[w];
 #pragma unroll
     for (int r = 0; r < RPT; ++r) {
-      sgdig[threadIdx.x * RPT + r] = run;
+      if (threadIdx.x * RPT + r < RADIX) sgdig[threadIdx.x * RPT + r] = run;
       run += loc[r];
     }
     __syncthreads();
@@ -331,7 +331,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(MapDev md, const Poin
       u32 tsum = 0;
 #pragma unroll
       for (int r = 0; r < RPT; ++r) {
-        loc[r] = scnt[threadIdx.x * RPT + r];
+        loc[r] = threadIdx.x * RPT + r < RADIX ? scnt[threadIdx.x * RPT + r] : 0u;
         tsum += loc[r];
       }
       u32 inc = tsum;
@@ -345,7 +345,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(MapDev md, const Poin
       for (int w = 0; w < warp; ++w) run += s_wsum[w];
 #pragma unroll
       for (int r = 0; r < RPT; ++r) {
-        sstart[threadIdx.x * RPT + r] = (int)run;
+        if (threadIdx.x * RPT + r < RADIX) sstart[threadIdx.x * RPT + r] = (int)run;
         run += loc[r];
       }
     }
@@ -1574,6 +1574,11 @@ __global__ void __launch_bounds__(kFT, 6) k_fuse_warps(MapDev md, const PointJob
     // pre-call state of the cell (the gate's), coordinates
     u32 fl = 0;
     float h0 = 0.f, v0 = 0.f, xs = 0.f, ys = 0.f, zs = 0.f;
+    u32 na0 = 0, nr0 = 0;  // pre-call counts of the cell, for the lane that ends the run's piece
+    if (on && (ed || tl)) {
+      na0 = md.n_acc[key];
+      nr0 = md.n_rej[key];
+    }
     if (on) {
       fl = md.flags[key];
       h0 = md.h[key];
@@ -1712,7 +1717,6 @@ __global__ void __launch_bounds__(kFT, 6) k_fuse_warps(MapDev md, const PointJob
       }
       const u32 nt = (u32)(t - max(ht, 0) + 1);  // points of the run in the tile
       const u32 g = key;
-      const u32 na0 = md.n_acc[g], nr0 = md.n_rej[g];
       if (ht >= 0 && ed) {
         // the whole run lies in the tile: every layer's rule, class max, height, flags
         const float N = (float)nt, rN = __frcp_rn(N);
