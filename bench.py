@@ -133,11 +133,16 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
+POINT_SOURCES = ("paper_2309_16818_gb300/csrc/mem_points.cu", "paper_2309_16818_gb300/csrc/mem_internal.cuh",
+                 "include/mem.h")
+
+
 def kernel_source_hash():
+    """First 12 hex digits of the SHA-256 of the point-path kernel sources (the translation
+    unit of its kernels and the headers it includes), in the order listed."""
     h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_2309_16818_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in POINT_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
     return h.hexdigest()[:12]
 
 
@@ -225,6 +230,9 @@ def run_ours(args):
         m.move(c["poses"][k][:2])
         m.fuse_pointcloud(xyz[k], c["scans"][k].T, [(rgb[k], [0]), (prb[k], [1, 2, 3])])
 
+    # summed columns of the call: 4 height sums, 3 colours, 20 classes + the class-max pair
+    fuse_columns = 4 + rgb[0].shape[1] + prb[0].shape[1] + 2
+
     # per-pose statistics (untimed): kept points and touched cells
     stats = []
     for k in range(n_pose):
@@ -310,7 +318,10 @@ def run_ours(args):
     per_launch_s = cand[dom] / 1e3 / launches.get(dom, K)
     peak, peak_kind = peaks()
     achieved = algo[dom] / per_launch_s / 1e9
-    ncu_name = {"fuse_tiles": "k_fuse_tiles", "radix_sort": "k_onesweep", "key": "k_points_key"}[dom]
+    # the fuse kernel of the call: per-cell sums in registers where its summed columns (4 height
+    # sums, every source's channels, an arg-max pair per class-max source) fit one round of 32
+    fuse_name = "k_fuse_warps" if m.get_tuning()["fuse_kernel"] == 0 and fuse_columns <= 32 else "k_fuse_tiles"
+    ncu_name = {"fuse_tiles": fuse_name, "radix_sort": "k_onesweep", "key": "k_points_key"}[dom]
     traffic = ncu_traffic(ncu_name)
     roofline = {"bound": "hbm", "kernel": ncu_name, "achieved": round(achieved, 1), "peak": peak,
                 "peak_kind": f"{peak_kind} (copy bandwidth)", "unit": "GB/s",
