@@ -871,8 +871,9 @@ def bench_image(args, dev, flush, ws, c2):
     return {"workload": "4 cameras 848x480, 64-d F32 + 64-d BF16 Gaussian features, 20-class Dirichlet + class max, 500x500 map",
             "ms_per_4_cameras": round(1e3 * t, 4), "camera_fuses_per_s": round(ws * 4 / t, 1),
             "cells_per_s": round(ws * 4 * c2["W"] ** 2 / t, 1), "visible_cells_per_camera": nvis,
-            "roofline": {"kernel": "k_image", "bound": "hbm (pixel gather and layer read-modify-write); the "
-                                                        "visibility walks run from L1/L2",
+            "roofline": {"kernel": "k_image_list + k_image_walk (one camera)",
+                         "bound": "hbm (pixel gather and layer read-modify-write); the visibility walks run "
+                                  "from L1/L2",
                          "us_per_launch": round(us_cam, 2), "algorithmic_bytes_per_launch": round(algo),
                          "achieved": round(algo / (us_cam / 1e6) / 1e9, 1), "unit": "GB/s", "peak": peak,
                          "frac": round(algo / (us_cam / 1e6) / 1e9 / peak, 4)}}

@@ -235,7 +235,9 @@ mem_status mem_fuse_pointcloud_batch(mem_map *m, const int64_t *offsets, const f
  * valid cell on the Bresenham line from the camera's cell lies strictly
  * below the ray. Visible cells fuse their pixel (one observation).
  * vis_out (uint8 [W*W]) and pix_out (int32 [W*W], py*Wi+px or -1) are
- * optional device outputs in logical cell order (row iy, column ix). */
+ * optional device outputs in logical cell order (row iy, column ix). The map
+ * allocates a list of W*W cells (12 bytes each) on the first call, which
+ * synchronises the stream. */
 mem_status mem_fuse_image(mem_map *m, int32_t map_index, int32_t H, int32_t Wi, int32_t n_sources,
                           const mem_source *sources, const double K[4], const double T_map_cam[16],
                           uint8_t *vis_out, int32_t *pix_out, void *stream);

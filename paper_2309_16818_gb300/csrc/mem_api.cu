@@ -515,6 +515,7 @@ extern "C" mem_status mem_destroy_map(mem_map* mm) {
   }
   if (m->copy_stream) cudaStreamDestroy(m->copy_stream);
   if (m->pca_buf) cudaFree(m->pca_buf);
+  if (m->img_buf) cudaFree(m->img_buf);
   for (cudaEvent_t e : m->prof_pool) cudaEventDestroy(e);
   delete mm;
   return MEM_OK;

@@ -64,6 +64,8 @@ struct Map {
   // scratch of the PCA plugin (grown on demand)
   void* pca_buf = nullptr;
   size_t pca_cap = 0;
+  void* img_buf = nullptr;  // image fusion: the list of cells to walk
+  size_t img_cap = 0;
   // allocations to free
   std::vector<void*> allocs;
   std::vector<void*> scratch_allocs;

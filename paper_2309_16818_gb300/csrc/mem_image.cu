@@ -4,14 +4,27 @@
 // strictly below the ray from the camera to the cell (equality occludes).
 // Visible cells fuse their pixel with the layer rules (one observation).
 //
-// A 16x16 tile of cells per block: the cells that need a visibility walk are
-// listed in shared memory and walked by consecutive threads (neighbouring
-// cells, so neighbouring lines read neighbouring heights through L1); each warp
-// then fuses its visible cells one at a time with its lanes spread over the
-// channels, so pixel rows and layer rows are read and written coalesced.
+// Three kernels: the cells that need a visibility walk are listed for the whole
+// map; consecutive threads walk consecutive listed cells' lines (neighbouring
+// cells, so neighbouring lines read neighbouring heights through L1) and list
+// the visible cells; every warp of a grid that fills the GPU then fuses visible
+// cells one at a time with its lanes spread over the channels, so pixel rows and
+// layer rows are read and written coalesced and the cells' chains of dependent
+// accesses run side by side.
 #include "mem_host.h"
 
 namespace memk {
+
+// the cells an image call lists for a visibility walk, then its visible cells
+// (capacity W * W each)
+struct ImgList {
+  u32* n;         // [0] listed cells, [1] visible cells
+  u32* cell;      // listed: y << 16 | x
+  float* hz;      // the cell's height
+  int32_t* pix;   // its pixel
+  u32* vg;        // visible: the cell's state index
+  int32_t* vp;    // its pixel
+};
 
 struct ImgParams {
   float R[9], t[3];  // map-centre frame -> optical camera frame
@@ -151,81 +164,104 @@ __device__ __forceinline__ void fuse_pixel_warp(const MapDev& md, const ImgParam
   if (lane == 0) md.flags[g] = fl;
 }
 
-// A block takes a 16 x 16 tile of cells: every thread projects its cell, the
-// cells that are valid, in front of the camera and inside the image are listed
-// in shared memory, and consecutive threads walk the listed cells' lines (the
-// others are done); each warp then fuses its visible cells' pixels.
-__global__ void __launch_bounds__(256) k_image(MapDev md, ImgParams ip, uint8_t* __restrict__ vis,
-                                               int32_t* __restrict__ pix) {
+// 1. Listing: a block takes a 16 x 16 tile of cells, every thread projects
+// its cell; the cells that are valid, in front of the camera and inside the
+// image are appended to one list for the whole map (a warp's cells together,
+// so neighbouring cells stay neighbours in the list); the others are done.
+__global__ void __launch_bounds__(256) k_image_list(MapDev md, ImgParams ip, ImgList li, uint8_t* __restrict__ vis,
+                                                    int32_t* __restrict__ pix) {
   const int W = md.W;
-  const int tid = threadIdx.y * 16 + threadIdx.x;
   const u32 base = (u32)ip.map_index * md.W2;
-  __shared__ int s_n;
-  __shared__ u32 s_cell[256];
-  __shared__ float s_hz[256];
-  __shared__ int32_t s_pix[256];
-  if (tid == 0) s_n = 0;
-  __syncthreads();
-  {
-    const int ix = blockIdx.x * 16 + threadIdx.x;
-    const int iy = blockIdx.y * 16 + threadIdx.y;
-    if (ix < W && iy < W) {
-      const u32 g = base + phys(md, ip.ring_x, ip.ring_y, ix, iy);
-      bool listed = false;
-      if (md.flags[g] & kFlagValid) {
-        const float xc = __fmul_rn(__fadd_rn((float)(ix - W / 2), 0.5f), md.res);
-        const float yc = __fmul_rn(__fadd_rn((float)(iy - W / 2), 0.5f), md.res);
-        const float hz = md.h[g];
-        const float Xc = __fmaf_rn(ip.R[0], xc, __fmaf_rn(ip.R[1], yc, __fmaf_rn(ip.R[2], hz, ip.t[0])));
-        const float Yc = __fmaf_rn(ip.R[3], xc, __fmaf_rn(ip.R[4], yc, __fmaf_rn(ip.R[5], hz, ip.t[1])));
-        const float Zc = __fmaf_rn(ip.R[6], xc, __fmaf_rn(ip.R[7], yc, __fmaf_rn(ip.R[8], hz, ip.t[2])));
-        if (Zc > md.z_near) {
-          const float u = __fmaf_rn(ip.fx, __fdiv_rn(Xc, Zc), ip.cx);
-          const float v = __fmaf_rn(ip.fy, __fdiv_rn(Yc, Zc), ip.cy);
-          const float fu = floorf(__fadd_rn(u, 0.5f));
-          const float fv = floorf(__fadd_rn(v, 0.5f));
-          if (fu >= 0.f && fu < (float)ip.Wi && fv >= 0.f && fv < (float)ip.H) {
-            const int k = atomicAdd(&s_n, 1);
-            s_cell[k] = ((u32)iy << 16) | (u32)ix;
-            s_hz[k] = hz;
-            s_pix[k] = (int32_t)((int64_t)fv * ip.Wi + (int64_t)fu);
-            listed = true;
-          }
+  const int lane = (threadIdx.y * 16 + threadIdx.x) & 31;
+  const int ix = blockIdx.x * 16 + threadIdx.x;
+  const int iy = blockIdx.y * 16 + threadIdx.y;
+  bool listed = false;
+  float hz = 0.f;
+  int32_t px = -1;
+  if (ix < W && iy < W) {
+    const u32 g = base + phys(md, ip.ring_x, ip.ring_y, ix, iy);
+    if (md.flags[g] & kFlagValid) {
+      const float xc = __fmul_rn(__fadd_rn((float)(ix - W / 2), 0.5f), md.res);
+      const float yc = __fmul_rn(__fadd_rn((float)(iy - W / 2), 0.5f), md.res);
+      hz = md.h[g];
+      const float Xc = __fmaf_rn(ip.R[0], xc, __fmaf_rn(ip.R[1], yc, __fmaf_rn(ip.R[2], hz, ip.t[0])));
+      const float Yc = __fmaf_rn(ip.R[3], xc, __fmaf_rn(ip.R[4], yc, __fmaf_rn(ip.R[5], hz, ip.t[1])));
+      const float Zc = __fmaf_rn(ip.R[6], xc, __fmaf_rn(ip.R[7], yc, __fmaf_rn(ip.R[8], hz, ip.t[2])));
+      if (Zc > md.z_near) {
+        const float u = __fmaf_rn(ip.fx, __fdiv_rn(Xc, Zc), ip.cx);
+        const float v = __fmaf_rn(ip.fy, __fdiv_rn(Yc, Zc), ip.cy);
+        const float fu = floorf(__fadd_rn(u, 0.5f));
+        const float fv = floorf(__fadd_rn(v, 0.5f));
+        if (fu >= 0.f && fu < (float)ip.Wi && fv >= 0.f && fv < (float)ip.H) {
+          listed = true;
+          px = (int32_t)((int64_t)fv * ip.Wi + (int64_t)fu);
         }
       }
-      if (!listed) {
-        const int64_t j = (int64_t)iy * W + ix;
-        if (vis) vis[j] = 0;
-        if (pix) pix[j] = -1;
-      }
+    }
+    if (!listed) {
+      const int64_t j = (int64_t)iy * W + ix;
+      if (vis) vis[j] = 0;
+      if (pix) pix[j] = -1;
     }
   }
-  __syncthreads();
-  const int n = s_n;
-  __shared__ int s_nv;
-  __shared__ u32 s_vg[256];
-  __shared__ int32_t s_vp[256];
-  if (tid == 0) s_nv = 0;
-  __syncthreads();
-  if (tid < n) {
-    const int ix = (int)(s_cell[tid] & 0xffffu), iy = (int)(s_cell[tid] >> 16);
-    const bool visible = walk_visible(md, base, ip.ring_x, ip.ring_y, ip.sx, ip.sy, ix, iy, s_hz[tid], ip.hc);
-    const int64_t j = (int64_t)iy * W + ix;
-    if (vis) vis[j] = visible ? 1 : 0;
-    if (pix) pix[j] = visible ? s_pix[tid] : -1;
-    if (visible && ip.n_src > 0) {
-      const int k = atomicAdd(&s_nv, 1);
-      s_vg[k] = base + phys(md, ip.ring_x, ip.ring_y, ix, iy);
-      s_vp[k] = s_pix[tid];
+  const u32 bal = __ballot_sync(0xffffffffu, listed);
+  u32 k0 = 0;
+  if (lane == 0 && bal) k0 = atomicAdd(li.n, (u32)__popc(bal));
+  k0 = __shfl_sync(0xffffffffu, k0, 0);
+  if (listed) {
+    const u32 k = k0 + (u32)__popc(bal & ((1u << lane) - 1u));
+    li.cell[k] = ((u32)iy << 16) | (u32)ix;
+    li.hz[k] = hz;
+    li.pix[k] = px;
+  }
+}
+
+// 2. Visibility over the list: consecutive threads walk consecutive listed
+// cells' lines (neighbouring cells, so neighbouring lines read neighbouring
+// heights through L1); visible cells are appended to the second list.
+__global__ void __launch_bounds__(256) k_image_walk(MapDev md, ImgParams ip, ImgList li, uint8_t* __restrict__ vis,
+                                                    int32_t* __restrict__ pix) {
+  const int W = md.W;
+  const u32 base = (u32)ip.map_index * md.W2;
+  const int n = (int)*li.n;
+  const int lane = threadIdx.x & 31;
+  for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {  // uniform per warp
+    const int i = i0 + threadIdx.x;
+    bool visible = false;
+    int32_t px = -1;
+    u32 gv = 0;
+    if (i < n) {
+      const u32 c = li.cell[i];
+      const int ix = (int)(c & 0xffffu), iy = (int)(c >> 16);
+      px = li.pix[i];
+      visible = walk_visible(md, base, ip.ring_x, ip.ring_y, ip.sx, ip.sy, ix, iy, li.hz[i], ip.hc);
+      const int64_t j = (int64_t)iy * W + ix;
+      if (vis) vis[j] = visible ? 1 : 0;
+      if (pix) pix[j] = visible ? px : -1;
+      gv = base + phys(md, ip.ring_x, ip.ring_y, ix, iy);
+    }
+    const u32 bal = __ballot_sync(0xffffffffu, visible);
+    u32 k0 = 0;
+    if (lane == 0 && bal) k0 = atomicAdd(li.n + 1, (u32)__popc(bal));
+    k0 = __shfl_sync(0xffffffffu, k0, 0);
+    if (visible) {
+      const u32 k = k0 + (u32)__popc(bal & ((1u << lane) - 1u));
+      li.vg[k] = gv;
+      li.vp[k] = px;
     }
   }
-  if (ip.n_src == 0) return;
-  __syncthreads();
-  // the visible cells dealt out to the block's warps, each fused by a whole warp
-  const int warp = tid >> 5, nwarps = (blockDim.x * blockDim.y) >> 5;
-  for (int v = warp; v < s_nv; v += nwarps) {
-    const u32 gv = s_vg[v];
-    fuse_pixel_warp(md, ip, gv, s_vp[v], md.flags[gv]);
+}
+
+// 3. Fusion: every warp of the grid takes visible cells in turn and fuses each
+// with its lanes spread over the channels (pixel rows and layer rows read and
+// written coalesced). Each cell is fused on its own, so the lists' order does
+// not change a result.
+__global__ void __launch_bounds__(128) k_image_fuse(MapDev md, ImgParams ip, ImgList li) {
+  const int nv = (int)li.n[1];
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < nv; v += nwarps) {
+    const u32 gv = li.vg[v];
+    fuse_pixel_warp(md, ip, gv, li.vp[v], md.flags[gv]);
   }
 }
 
@@ -263,9 +299,32 @@ cudaError_t launch_image_fuse(Map* m, int map_index, const MapCall& mc, int H, i
   ip.ring_y = mc.ring_y;
   ip.n_src = n_src;
   for (int q = 0; q < n_src; ++q) ip.src[q] = src[q];
-  dim3 blk(16, 16), grd((md.W + 15) / 16, (md.W + 15) / 16);
+  // the list (one map's cells at most), allocated on the first call
+  const size_t need = sizeof(u32) * (4 + 5 * (size_t)md.W2);
+  if (need > m->img_cap) {
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return e;
+    if (m->img_buf) cudaFree(m->img_buf);
+    m->img_buf = nullptr;
+    m->img_cap = 0;
+    e = cudaMalloc(&m->img_buf, need);
+    if (e != cudaSuccess) return e;
+    m->img_cap = need;
+  }
+  ImgList li;
+  li.n = (u32*)m->img_buf;
+  li.cell = li.n + 4;
+  li.hz = (float*)(li.cell + md.W2);
+  li.pix = (int32_t*)(li.hz + md.W2);
+  li.vg = (u32*)(li.pix + md.W2);
+  li.vp = (int32_t*)(li.vg + md.W2);
   ProfScope ps(m, kProfImage, st);
-  k_image<<<grd, blk, 0, st>>>(md, ip, vis, pix);
+  cudaError_t e = cudaMemsetAsync(li.n, 0, 2 * sizeof(u32), st);
+  if (e != cudaSuccess) return e;
+  dim3 blk(16, 16), grd((md.W + 15) / 16, (md.W + 15) / 16);
+  k_image_list<<<grd, blk, 0, st>>>(md, ip, li, vis, pix);
+  k_image_walk<<<m->n_sm * 8, 128, 0, st>>>(md, ip, li, vis, pix);
+  if (n_src > 0) k_image_fuse<<<m->n_sm * 16, 128, 0, st>>>(md, ip, li);
   return cudaGetLastError();
 }
 
