@@ -9,6 +9,18 @@
 // Unknown cells start from the mean of the crop's known cells; the sweeps stop
 // when the largest update of a full sweep falls below `tol` or after
 // `max_iters` sweeps.
+//
+// Over-relaxation factor: SOR with the optimal factor for the Jacobi spectral
+// radius mu of the unknown region, omega = 2 / (1 + sqrt(1 - mu^2)), shrinks
+// the error by omega - 1 per sweep (the classical red-black SOR theory of
+// consistently ordered matrices). The shared-memory kernel bounds mu per crop
+// from d, the largest Euclidean distance from an unknown cell to the nearest
+// known cell (zero-flux crop borders mirror the region, so they do not bound
+// it): a strip of width 2 d has the smallest Laplacian eigenvalue
+// (pi / (2 d))^2, so mu <= 1 - (pi / (2 d))^2 / 4 is taken, which errs towards
+// over-relaxation, where the rate degrades only linearly. The factor is capped
+// at that of a square crop with fixed borders, sized by its longer side (the
+// factor the global-memory kernel uses for every crop).
 #include <cooperative_groups.h>
 #include <math.h>
 
@@ -187,9 +199,68 @@ __global__ void __launch_bounds__(kInpThreads) k_inpaint_sor_cluster(int H, int 
   uint8_t* Kn = (uint8_t*)(sh + 2 * (size_t)rows_max * Wh);
   uint8_t* K[2] = {Kn, Kn + (size_t)rows_max * Wh};
   __shared__ float red[33];
-  __shared__ float s_part[2];
+  __shared__ float s_part[3];
   __shared__ float s_dm[2];
   __shared__ int s_ne[2];
+  // 0. the squared largest distance of an unknown cell to a known cell: first, per row of
+  //    the band, the distance along the row (kFar: none), in the heights' shared memory
+  //    (free until they are loaded); then per unknown cell of the band the exact Euclidean
+  //    distance over the column (rows of the other bands read from their CTAs), scanning
+  //    outwards until no closer known cell can remain
+  constexpr int kFar = 0x3fff;
+  uint16_t* gd = reinterpret_cast<uint16_t*>(sh);  // [rows][W]
+  {
+    const int64_t b0 = (int64_t)crop * H * W + (int64_t)y0 * W;
+    for (int ly = threadIdx.x; ly < rows; ly += blockDim.x) {
+      const uint8_t* kr = known + b0 + (int64_t)ly * W;
+      uint16_t* gr = gd + (size_t)ly * W;
+      int last = -kFar;
+      for (int x = 0; x < W; ++x) {
+        if (kr[x]) last = x;
+        gr[x] = (uint16_t)min(x - last, kFar);
+      }
+      last = 0x3fffffff;
+      for (int x = W - 1; x >= 0; --x) {
+        if (kr[x]) last = x;
+        gr[x] = (uint16_t)min((int)gr[x], last - x);
+      }
+    }
+  }
+  cl.sync();
+  {
+    const int64_t b0 = (int64_t)crop * H * W + (int64_t)y0 * W;
+    int best_all = 0;
+    for (int j = threadIdx.x; j < rows * W; j += blockDim.x) {
+      if (known[b0 + j]) continue;
+      const int ly = j / W, x = j - ly * W;
+      const int y = y0 + ly;
+      const int g0 = gd[j];
+      int best = g0 * g0;
+      int q = r;  // band of the row read last (rows are read moving away from y)
+      int qd = r;
+      // (a cell whose distance can no longer exceed this thread's largest stops early)
+      for (int k = 1; k * k < best && best > best_all; ++k) {
+        const bool up = y - k >= 0, dn = y + k < H;
+        if (!up && !dn) break;
+        if (up) {
+          const int yy = y - k;
+          while ((int)((int64_t)H * q / CL) > yy) --q;
+          const int g = cl.map_shared_rank(gd, q)[(size_t)(yy - (int)((int64_t)H * q / CL)) * W + x];
+          best = min(best, g * g + k * k);
+        }
+        if (dn) {
+          const int yy = y + k;
+          while ((int)((int64_t)H * (qd + 1) / CL) <= yy) ++qd;
+          const int g = cl.map_shared_rank(gd, qd)[(size_t)(yy - (int)((int64_t)H * qd / CL)) * W + x];
+          best = min(best, g * g + k * k);
+        }
+      }
+      best_all = max(best_all, best);
+    }
+    const float dm2 = block_max((float)best_all, red);
+    if (threadIdx.x == 0) s_part[2] = dm2;
+  }
+  cl.sync();  // every band's distances are read; the heights may overwrite them
   // border cells of the crop (fewer than four neighbours) per colour, as ly << 16 | k
   u32* elist[2] = {(u32*)(Kn + ((2 * (size_t)rows_max * Wh + 3) & ~(size_t)3)), nullptr};
   const int ecap = 2 * rows_max + 2 * Wh + 2;  // one or two edge cells per row, the first and last rows
@@ -220,13 +291,20 @@ __global__ void __launch_bounds__(kInpThreads) k_inpaint_sor_cluster(int H, int 
     s_part[1] = c;
   }
   cl.sync();
-  float S = 0.f, Cn = 0.f;
+  float S = 0.f, Cn = 0.f, D2 = 0.f;
   for (int q = 0; q < CL; ++q) {
     const float* pp = cl.map_shared_rank(s_part, q);
     S += pp[0];
     Cn += pp[1];
+    D2 = fmaxf(D2, pp[2]);
   }
   const float mean = Cn > 0.f ? S / Cn : 0.f;
+  {  // the crop's over-relaxation factor from the distance bound (at least one cell apart)
+    const float d = fmaxf(sqrtf(D2), 1.f);
+    const float a = 3.14159265f / (2.f * d);
+    const float lq = 0.25f * a * a;  // 1 - mu
+    omega = fminf(omega, 2.f / (1.f + sqrtf(lq * (2.f - lq))));
+  }
   for (int q = 0; q < 2; ++q)
     for (int j = threadIdx.x; j < rows * Wh; j += blockDim.x)
       if (!(K[q][j] & 1)) A[q][j] = mean;
@@ -326,7 +404,8 @@ extern "C" mem_status mem_inpaint_diffusion(int32_t n_crops, int32_t H, int32_t 
   if (n_crops > 0 && (!h_in || !known || !h_out)) return memh::api_fail(MEM_ERR_ARG, "NULL argument");
   if (!(tol > 0.f) || max_iters < 1) return memh::api_fail(MEM_ERR_ARG, "tol > 0 and max_iters >= 1");
   if (n_crops == 0) return MEM_OK;
-  // optimal over-relaxation of the model problem on the longer side
+  // optimal over-relaxation of a square crop with fixed borders on the longer side (the
+  // shared-memory kernel lowers it per crop from the crop's unknown region)
   const int L = H > W ? H : W;
   const float omega = (float)(2.0 / (1.0 + sin(M_PI / (double)(L + 1))));
   const int CL = sor_cluster_size(H, W);

@@ -40,6 +40,23 @@ def test_diffusion_inpainting_matches_exact_solution(torch, size, n):
         assert np.array_equal(out[b][k[b] == 1], hin[b][k[b] == 1])
 
 
+def test_diffusion_per_crop_relaxation_cuts_sweeps(torch):
+    """The shared-memory fill sizes its over-relaxation per crop from the largest distance of an
+    unknown cell to a known one. On occlusion-hole crops of 256 x 256 the fixed factor of a
+    256-cell square needs ~500-540 sweeps per crop (its error shrinks by omega - 1 = 0.976 per
+    sweep whatever the holes); the per-crop factor must need far fewer, never more than the
+    fixed one, and still reach the exact solution."""
+    from paper_2309_16818_gb300 import mem as M
+    h, k = synth.inpaint_crops(8, size=256, seed=7)
+    out, its = M.inpaint_diffusion(torch.from_numpy(h).cuda(), torch.from_numpy(k).cuda(), tol=1e-6)
+    its = its.cpu().numpy()
+    out = out.cpu().numpy()
+    assert its.max() <= 560 and its.mean() < 350, its
+    for b in range(2):
+        ex = O.harmonic_fill_exact(h[b], k[b])
+        assert np.abs(out[b] - ex).max() < 1e-6 * 256, b
+
+
 def test_diffusion_edge_cases(torch):
     from paper_2309_16818_gb300 import mem as M
     # all known: unchanged; none known: every cell keeps the mean (0); 1 x 1 and ragged sizes
