@@ -307,7 +307,9 @@ def run_ours(args):
         # layer of every touched cell read and written
         "fuse_tiles": kept * (4 + 4 + 12 + payload) + cells * cb,
     }
-    launches = {"key": K, "radix_sort": K * P, "fuse_tiles": K, "fuse_cross": K, "move": prof["move"][1]}
+    # the warp fuse kernel fuses the runs that cross tiles itself (no k_fuse_cross launch)
+    launches = {"key": K, "radix_sort": K * P, "fuse_tiles": K, "fuse_cross": prof["fuse_cross"][1],
+                "move": prof["move"][1]}
     kern = {}
     for name, (ms, calls) in prof.items():
         if calls:
@@ -369,8 +371,23 @@ def run_ours(args):
         eb.record(stream)
         torch.cuda.synchronize()
         e_s = max_over_ranks(ea.elapsed_time(eb) / 1e3, ws)
+        # the host link's own rate for the same bytes: one page-locked host-to-device copy of a
+        # step's upload (the cloud's three arrays in one buffer), best of 5, CUDA events
+        hb = torch.empty(int(h2d / K), dtype=torch.uint8).pin_memory()
+        db = torch.empty(int(h2d / K), dtype=torch.uint8, device=dev)
+        link = []
+        for _ in range(5):
+            la, lb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            la.record(stream)
+            db.copy_(hb, non_blocking=True)
+            lb.record(stream)
+            torch.cuda.synchronize()
+            link.append(la.elapsed_time(lb) / 1e3)
+        link_gbs = hb.numel() / min(link) / 1e9
         e2e = {"value": round(ws * e_pts / e_s, 1), "unit": UNIT, "h2d_bytes_per_step": int(h2d / K),
                "d2h_bytes_per_step": int(d2h / K),
+               "h2d_link_gbs": round(link_gbs, 1),
+               "h2d_bound_points_per_s": round(ws * link_gbs * 1e9 / (12 + 3 + 80), 1),
                "note": "mem_fuse_pointcloud_host: page-locked host cloud uploaded each step (10 poses, "
                        "540 MB of distinct host data cycled), move + fuse, height layer read back to "
                        "page-locked host memory each step; whole-run throughput, no L2 flush inside"}
@@ -871,7 +888,7 @@ def bench_image(args, dev, flush, ws, c2):
     return {"workload": "4 cameras 848x480, 64-d F32 + 64-d BF16 Gaussian features, 20-class Dirichlet + class max, 500x500 map",
             "ms_per_4_cameras": round(1e3 * t, 4), "camera_fuses_per_s": round(ws * 4 / t, 1),
             "cells_per_s": round(ws * 4 * c2["W"] ** 2 / t, 1), "visible_cells_per_camera": nvis,
-            "roofline": {"kernel": "k_image_list + k_image_walk (one camera)",
+            "roofline": {"kernel": "k_image_list + k_image_walk + k_image_fuse (one camera)",
                          "bound": "hbm (pixel gather and layer read-modify-write); the visibility walks run "
                                   "from L1/L2",
                          "us_per_launch": round(us_cam, 2), "algorithmic_bytes_per_launch": round(algo),

@@ -288,7 +288,11 @@ static cudaError_t ensure_partial(Map* m, int acc) {
 cudaError_t launch_clear_entering(Map* m, int map_index, int sx, int sy, int ring_x, int ring_y,
                                   cudaStream_t st) {
   ProfScope ps(m, kProfMove, st);
-  k_reset<<<m->n_sm * 4, 256, 0, st>>>(m->md, map_index, sx, sy, ring_x, ring_y);
+  // one thread per entering cell (the strips: |sx| columns and |sy| rows), at most 4 blocks per SM
+  const int64_t W = m->md.W;
+  const int64_t cells = (std::min<int64_t>(std::abs(sx), W) + std::min<int64_t>(std::abs(sy), W)) * W;
+  const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((int64_t)m->n_sm * 4, (cells + 255) / 256));
+  k_reset<<<(unsigned)blocks, 256, 0, st>>>(m->md, map_index, sx, sy, ring_x, ring_y);
   return cudaGetLastError();
 }
 
