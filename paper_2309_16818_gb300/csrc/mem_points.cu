@@ -458,6 +458,7 @@ constexpr int kSegMax = 32;     // segments of a tile per walk
 constexpr int kStageU = 6;      // staging chunks in flight per thread
 constexpr int kStageV = 5;      // float4 row loads in flight per thread (warp fuse kernel)
 constexpr int kApplyU = 4;      // rule tasks in flight per thread
+constexpr int kCrossU = 8;      // slot pieces in flight per lane (runs crossing tiles)
 constexpr u32 kBitHead = 1u;    // slot bits: the run begins in the tile
 constexpr u32 kBitEnd = 2u;     //            the run ends in the tile
 constexpr u32 kBitUsed = 4u;    //            the slot holds a piece of this call
@@ -1250,27 +1251,8 @@ __device__ __forceinline__ void cross_run(const MapDev& md, const LayerDev* sL, 
 #pragma unroll
     for (int j = 0; j < kApplyU; ++j) old[j] = s02[j] = 0.f;
     if (gc < G) {
-      // four pieces' loads in flight, added in tile order
-      for (int p0 = 0; p0 < np; p0 += 4) {
-        float v[4], w[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          v[u] = 0.f;
-          w[u] = __int_as_float(0x7fffffff);
-          if (p0 + u < np) {
-            const float* sl = fz_slot(md, acc, h + p0 + u, h + p0 + u == last ? 0 : 1) + slot_off(gc);
-            v[u] = __ldcg(sl);
-            if (ch == kChArgV) w[u] = __ldcg(sl + 1);
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          if (p0 + u < np) {
-            S += v[u];
-            if (ch == kChArgV) m = cm_comb(m, make_float2(v[u], w[u]));
-          }
-        }
-      }
+      // the column's old layer values first (independent of the sums), then the pieces,
+      // kCrossU loads in flight, added in tile order
       if (q >= 0 && ch >= 0) {
 #pragma unroll
         for (int j = 0; j < kApplyU; ++j) {
@@ -1281,6 +1263,26 @@ __device__ __forceinline__ void cross_run(const MapDev& md, const LayerDev* sL, 
               if (L.rule != MEM_RULE_LATEST) old[j] = ld_layer(L, (int64_t)g * L.S + ch);
               if (L.rule == MEM_RULE_GAUSS) s02[j] = L.gvar[g];
             }
+          }
+        }
+      }
+      for (int p0 = 0; p0 < np; p0 += kCrossU) {
+        float v[kCrossU], w[kCrossU];
+#pragma unroll
+        for (int u = 0; u < kCrossU; ++u) {
+          v[u] = 0.f;
+          w[u] = __int_as_float(0x7fffffff);
+          if (p0 + u < np) {
+            const float* sl = fz_slot(md, acc, h + p0 + u, h + p0 + u == last ? 0 : 1) + slot_off(gc);
+            v[u] = __ldcg(sl);
+            if (ch == kChArgV) w[u] = __ldcg(sl + 1);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < kCrossU; ++u) {
+          if (p0 + u < np) {
+            S += v[u];
+            if (ch == kChArgV) m = cm_comb(m, make_float2(v[u], w[u]));
           }
         }
       }
